@@ -1,0 +1,204 @@
+/*
+ * lrnr.h -- C ABI of the GB300 (sm_103a) FastLRNR / sparse physics-informed
+ * backpropagation library (liblrnr.so).
+ *
+ * The library evaluates a low rank neural representation (LRNR) and its
+ * EIM-reduced form (FastLRNR) at many collocation points, carries the input
+ * derivatives u, u_t, u_x, u_xx forward with it, forms the convection-diffusion-
+ * reaction residual and physics-informed loss, and returns the exact gradient of
+ * that loss with respect to the coefficients s and the biases b.
+ *
+ * Notation (paper: "FastLRNR and Sparse Physics Informed Backpropagation").
+ *   L      number of activated (hidden) layers; the network has L+1 weight layers
+ *          l = 0..L (the paper's 1..L+1, Sec. 2.1 Eq. 2.1).
+ *   M      hidden width; input width 2 (x, t), output width 1 (u) (Sec. 2.1).
+ *   r[l]   rank of weight layer l, W^l = U^l diag(s^l) V^l^T (Sec. 2.1 Eq. 2.2).
+ *          U^l is M_l x r[l], V^l is M_{l-1} x r[l] (V has as many rows as the
+ *          layer's input; the printed M_l rows cannot multiply z^{l-1}).
+ *          Constraints: 1 <= r[0] <= 2, 1 <= r[l] <= 32 for 0 < l < L, r[L] == 1.
+ *   s      coefficients, per PDE instance a vector of sum(r) floats, layer-major.
+ *   b      biases, b^l of length M_l; sum over layers = L*M + 1 ("sum_m").
+ *   mu     (beta, nu, rho): N[u] = u_t + beta u_x - nu u_xx - rho u (1-u)
+ *          on (0, 2pi) x (0, 1), u(x,0) = sin x, u(0,t) = u(2pi,t) (Sec. 4 Eq. 4.1).
+ *
+ * Conventions.
+ *   Memory: every pointer documented "device" is caller-owned CUDA device memory
+ *     on the model's device; "host" pointers are ordinary host memory.  The
+ *     library owns only the model handle, its packed copies of the bases and a
+ *     workspace for per-tile partial sums (grown by lrnr_reserve or on first use).
+ *   Streams: every launch goes on the given cudaStream_t (passed as void*; NULL
+ *     = legacy default stream).  lrnr_residual, lrnr_residual_grad and
+ *     spinprop_step do no host synchronisation and can be captured in a CUDA graph
+ *     once the workspace is large enough (otherwise they return LRNR_ENOTREADY
+ *     while the stream is capturing).  fastlrnr_select_rows synchronises.
+ *   Errors: functions return a status and never abort.  Launch failures return
+ *     LRNR_ECUDA; errors found by kernels (non-finite inputs, iteration caps) are
+ *     recorded in a device status word read by lrnr_last_device_status.
+ *   Concurrency: calls on one model share its workspace and must be ordered
+ *     (one stream, or explicit events).
+ */
+#ifndef LRNR_H
+#define LRNR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRNR_OK = 0,
+  LRNR_EINVAL = 1,      /* bad argument: null pointer, size or rank out of range */
+  LRNR_ENOMEM = 2,      /* device allocation failed */
+  LRNR_ECUDA = 3,       /* a CUDA call or kernel launch failed */
+  LRNR_ESINGULAR = 4,   /* EIM: the interpolation block P^T Xi is singular */
+  LRNR_EEARLYSTOP = 5,  /* reserved: EIM stop is reported through rhat_used */
+  LRNR_ETIMEOUT = 6,    /* a device wait reached its iteration cap */
+  LRNR_ENOTREADY = 7,   /* FastLRNR layers not selected, or workspace too small while capturing */
+  LRNR_ENONFINITE = 8,  /* a kernel met a NaN or infinity in its input */
+  LRNR_ENOTSUP = 9      /* the (form, precision) pair is not implemented */
+} lrnr_status;
+
+typedef enum {
+  LRNR_FP32 = 0,        /* FP32 SIMT everywhere (reference precision of the GPU path) */
+  LRNR_TF32 = 1,        /* reserved */
+  LRNR_BF16 = 2,        /* full form: tcgen05 BF16 operands, FP32 accumulation in TMEM */
+  LRNR_BF16X3 = 3       /* full form: split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+} lrnr_precision;
+
+typedef enum { LRNR_FULL = 0, LRNR_FAST = 1 } lrnr_form;
+typedef enum { LRNR_LOSS_MSE = 0, LRNR_LOSS_L1 = 1 } lrnr_loss;
+
+typedef struct lrnr_model lrnr_model;
+
+/*
+ * A batch of PDE instances and their collocation points (Sec. 3.2 Eq. 3.5-3.6,
+ * Sec. 4 Eq. 4.1).  All arrays are device memory; instance i owns the points
+ * [off[i], off[i+1]) of each class.  Totals are host values and must equal
+ * int_off[n_inst], ic_off[n_inst], bc_off[n_inst].
+ */
+typedef struct {
+  int32_t n_inst;                 /* number of instances (mu, s pairs), >= 1 */
+  int64_t n_int, n_ic, n_bc;      /* host: total interior points, initial points, periodic pairs */
+  const float *beta, *nu, *rho;   /* device [n_inst]: mu = (beta, nu, rho) */
+  const float *s;                 /* device [n_inst][sum_r]: coefficients (ignored by spinprop_step) */
+  const int64_t *int_off;         /* device [n_inst+1] CSR offsets into x_int/t_int */
+  const int64_t *ic_off;          /* device [n_inst+1] offsets into x_ic */
+  const int64_t *bc_off;          /* device [n_inst+1] offsets into t_bc */
+  const float *x_int, *t_int;     /* device [n_int]: interior points (x, t) */
+  const float *x_ic;              /* device [n_ic]: initial points (x, 0), target sin x */
+  const float *t_bc;              /* device [n_bc]: periodic pairs (0, t) and (2pi, t) */
+} lrnr_batch;
+
+/*
+ * lrnr_build -- create a model from frozen bases (U*, V*, b*) (Sec. 2.1 Eq. 2.4).
+ *   L, M : hidden layers (1..16) and width (1..4096).
+ *   r    : host [L+1] ranks (constraints above).
+ *   U, V, b : host arrays of L+1 pointers to row-major FP64 matrices
+ *          U[l]: M_l x r[l], V[l]: M_{l-1} x r[l], b[l]: M_l, with M_{-1} = 2,
+ *          M_l = M for l < L and M_L = 1.  Copied; the caller keeps ownership.
+ *   out  : receives the handle (on the current CUDA device).
+ * Returns LRNR_EINVAL for bad sizes or null pointers, LRNR_ENOMEM / LRNR_ECUDA.
+ */
+lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U,
+                       const double *const *V, const double *const *b, lrnr_model **out);
+
+/*
+ * lrnr_snapshots -- FP64 hidden states z^layer = tanh(U s V^T z + b) of the exact
+ * LRNR (the EIM snapshots of Sec. 4) at n_pts points for n_s coefficient draws.
+ *   layer : hidden layer 0..L-1.
+ *   x, t  : device FP64 [n_pts].  s: device FP64 [n_s][sum_r].
+ *   out   : device FP64, M x (n_s*n_pts), column-major; column j*n_pts + p holds
+ *           the state for draw j at point p.
+ */
+lrnr_status lrnr_snapshots(lrnr_model *m, int layer, int64_t n_pts, const double *x,
+                           const double *t, int n_s, const double *s, double *out,
+                           void *stream);
+
+/*
+ * fastlrnr_select_rows -- EIM row selection for hidden layer `layer` and
+ * installation of its reduced bases (Sec. 2.2 Eq. 2.7-2.8):
+ *   Uhat = P^T U^l, bhat = P^T b^l, Vhat = (P^T Xi)^{-T} Xi^T V^{l+1}.
+ * Greedy (rows_in == NULL): classic EIM on `snapshots` (device FP64, M x K,
+ *   column-major, not modified), at most `rhat` (1..32) steps; picks the column
+ *   with the largest max-abs residual and, in it, the row of largest |value|
+ *   (lowest index on exact ties); stops early when that max-abs <= tol (absolute).
+ *   FP64 throughout, no fused multiply-add in the residual update, so the rows
+ *   match an IEEE FP64 reference bit for bit.
+ * Given (rows_in != NULL): device int32 [rhat] distinct rows and Xi_in, device
+ *   FP64 M x rhat column-major; P^T Xi must be invertible (LRNR_ESINGULAR).
+ * Outputs: rows_out (device int32 [rhat], may be NULL), Xi_out (device FP64
+ *   M x rhat column-major, may be NULL), *rhat_used (host) = rows kept.
+ * Synchronises `stream`.  After every layer 0..L-1 has been selected, LRNR_FAST
+ * calls are allowed.
+ */
+lrnr_status fastlrnr_select_rows(lrnr_model *m, int layer, const double *snapshots, int64_t K,
+                                 int rhat, double tol, const int32_t *rows_in,
+                                 const double *Xi_in, int32_t *rows_out, double *Xi_out,
+                                 int *rhat_used, void *stream);
+
+/*
+ * lrnr_residual -- forward only (Sec. 2.1 Eq. 2.1 / Sec. 2.2 Eq. 2.8 and Eq. 4.1).
+ * Writes, for interior points, u, u_t, u_x, u_xx and the residual N[u] (device
+ * FP32 [n_int] each), the initial residual u(x,0) - sin x (device [n_ic]) and the
+ * periodic residual u(0,t) - u(2pi,t) (device [n_bc]).  Any output may be NULL.
+ */
+lrnr_status lrnr_residual(lrnr_model *m, lrnr_form form, lrnr_precision prec,
+                          const lrnr_batch *bt, float *u, float *u_t, float *u_x, float *u_xx,
+                          float *res, float *res_ic, float *res_bc, void *stream);
+
+/*
+ * lrnr_residual_grad -- loss and exact gradient per instance (Sec. 2.3, Eq. 3.5 /
+ * Eq. 3.6).  MSE: w0 mean R^2 + w1 mean B_ic^2 + w2 mean B_bc^2 (a term with no
+ * points is absent); L1: w0 sum|R| + w1 sum|B_ic| + w2 sum|B_bc| (sign(0) = 0).
+ *   w        : host float[3] or NULL (= 1, 1, 1).
+ *   loss_out : device [n_inst].  dL_ds: device [n_inst][sum_r].
+ *   dL_db    : device [n_inst][sum_m] or NULL; FastLRNR puts the gradient of the
+ *              kept rows at their positions and zero elsewhere.
+ * Results are deterministic: partial sums are reduced in a fixed order.
+ */
+lrnr_status lrnr_residual_grad(lrnr_model *m, lrnr_form form, lrnr_precision prec,
+                               const lrnr_batch *bt, lrnr_loss loss, const float *w,
+                               float *loss_out, float *dL_ds, float *dL_db, void *stream);
+
+/*
+ * spinprop_step -- n_steps Adam steps on s (Sec. 3.2 Eq. 3.6-3.7, Sec. 4), each a
+ * fused residual + gradient pass followed by the update
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   s -= lr (m / (1 - b1^k)) / (sqrt(v / (1 - b2^k)) + eps),   k = ++(*step),
+ * with g = dL/ds + lambda_loc sign(s - s_anchor) when s_anchor != NULL.
+ *   s_inout, adam_m, adam_v : device [n_inst][sum_r] (bt->s is ignored).
+ *   step     : device int64 [1], Adam step count, incremented on the device.
+ *   loss_out : device [n_inst] or NULL: loss (with the locality term) of the last step.
+ */
+lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec,
+                          const lrnr_batch *bt, lrnr_loss loss, const float *w,
+                          float *s_inout, float *adam_m, float *adam_v, int64_t *step,
+                          int n_steps, float lr, float beta1, float beta2, float eps,
+                          float lambda_loc, const float *s_anchor, float *loss_out,
+                          void *stream);
+
+/* lrnr_reserve -- size the workspace for batches of up to max_points collocation
+ * points (interior + initial + 2 x pairs) in up to max_inst instances.  Call it
+ * before capturing a CUDA graph. */
+lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst);
+
+/* lrnr_model_info -- host outputs (any may be NULL): L, M, sum_r, sum_m and
+ * whether every hidden layer has reduced bases (fast_ready). */
+lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int *sum_m,
+                            int *fast_ready);
+
+/* lrnr_last_device_status -- synchronises the device, returns and clears the
+ * status word written by kernels (LRNR_OK if none). */
+lrnr_status lrnr_last_device_status(lrnr_model *m);
+
+const char *lrnr_status_string(lrnr_status s);
+
+void lrnr_destroy(lrnr_model *m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRNR_H */

@@ -1,0 +1,605 @@
+// C ABI of liblrnr.so: argument validation, model and workspace management, and
+// the launch sequences of each entry point.  See include/lrnr.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lrnr_internal.cuh"
+
+namespace lrnr {
+cudaError_t launch_eim_reduce_f64(const double *Xi, const int32_t *rows, int rh, int M,
+                                  const double *U, const double *b, const double *Vn, int rin,
+                                  int rout, double *out, int *status, cudaStream_t st);
+cudaError_t launch_snapshots_f64(const double *w64, int L, int M, const int *r_dev,
+                                 const int64_t *offs_dev, int layer, int64_t n_pts,
+                                 const double *x, const double *t, int n_s, const double *s,
+                                 int sum_r, double *out, cudaStream_t st);
+int full_tc_supported(int L, int M, int RM);
+size_t full_tc_pack_bytes(int L, int M, int RM);
+void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &U,
+                  const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
+                  const int *r, std::vector<unsigned char> &out);
+int full_tc_nt();
+}  // namespace lrnr
+
+using namespace lrnr;
+
+struct lrnr_model {
+  int device = 0;
+  int num_sms = 1;
+  int L = 0, M = 0;
+  int r[LMAX + 1] = {0};
+  int roff[LMAX + 2] = {0};
+  int sum_r = 0, sum_m = 0;
+  int RM = 8;
+  std::vector<std::vector<double>> U, V, b;   // host FP64 bases
+  float *full_pack = nullptr;                  // FP32, full form
+  double *w64 = nullptr;                       // FP64 bases (snapshots)
+  int *r_dev = nullptr;
+  int64_t *offs_dev = nullptr;
+  void *tc_pack = nullptr;                     // tensor-core operand pack (full form)
+  // reduced layers (host, FP64): Uh [rh][r_l], bh [rh], Vh [rh][r_{l+1}], rows [rh]
+  int rhat[LMAX] = {0};
+  std::vector<std::vector<double>> Uh, bh, Vh;
+  std::vector<std::vector<int32_t>> rows;
+  bool fast_dirty = true;
+  int fRM = 0, fRH = 0;
+  float *fast_pack = nullptr;
+  int32_t *rows_dev = nullptr;
+  int *status_dev = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace {
+
+lrnr_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LRNR_OK;
+  if (e == cudaErrorMemoryAllocation) return LRNR_ENOMEM;
+  return LRNR_ECUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+int pad_rank(int r) { return r <= 8 ? 8 : (r <= 16 ? 16 : 32); }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Available (RM, RH) instantiations of the FastLRNR kernel, cheapest first.
+const int kFastPairs[][2] = {{8, 16}, {16, 16}};
+
+int64_t max_tiles(int64_t n_int, int64_t n_ic, int64_t n_bc, int n_inst, int nt) {
+  return (n_int + nt - 1) / nt + (n_ic + nt - 1) / nt + (n_bc + nt / 2 - 1) / (nt / 2) +
+         3 * (int64_t)n_inst;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+lrnr_status ensure_ws(lrnr_model *m, size_t need, cudaStream_t st) {
+  if (m->ws_bytes >= need) return LRNR_OK;
+  if (capturing(st)) return LRNR_ENOTREADY;
+  if (m->ws) {
+    CK(cudaStreamSynchronize(st));
+    CK(cudaFree(m->ws));
+    m->ws = nullptr;
+    m->ws_bytes = 0;
+  }
+  CK(cudaMalloc(&m->ws, need));
+  m->ws_bytes = need;
+  return LRNR_OK;
+}
+
+lrnr_status build_fast_pack(lrnr_model *m) {
+  if (!m->fast_dirty) return LRNR_OK;
+  int need_rh = 0;
+  for (int l = 0; l < m->L; ++l) {
+    if (m->rhat[l] <= 0) return LRNR_ENOTREADY;
+    need_rh = std::max(need_rh, m->rhat[l]);
+  }
+  int RMp = 0, RHp = 0;
+  for (auto &pr : kFastPairs)
+    if (pr[0] >= m->RM && pr[1] >= need_rh) { RMp = pr[0]; RHp = pr[1]; break; }
+  if (!RMp) return LRNR_ENOTSUP;
+  const int L = m->L;
+  const int LS = fast_layer_floats(RMp, RHp);
+  std::vector<float> pk((size_t)fast_pack_floats(L, RMp, RHp), 0.0f);
+  std::vector<int32_t> rw((size_t)L * RHp, -1);
+  for (int l = 0; l < L; ++l) {
+    const int rh = m->rhat[l], rin = m->r[l], rout = m->r[l + 1];
+    float *Uh = pk.data() + (size_t)l * LS, *bh = Uh + RHp * RMp, *Vh = bh + RHp;
+    for (int a = 0; a < rh; ++a) {
+      for (int k = 0; k < rin; ++k) Uh[a * RMp + k] = (float)m->Uh[l][(size_t)a * rin + k];
+      bh[a] = (float)m->bh[l][a];
+      for (int k = 0; k < rout; ++k) Vh[a * RMp + k] = (float)m->Vh[l][(size_t)a * rout + k];
+      rw[(size_t)l * RHp + a] = m->rows[l][a];
+    }
+  }
+  float *tail = pk.data() + (size_t)L * LS;
+  for (int k = 0; k < m->r[0]; ++k) {
+    tail[k] = (float)m->V[0][k];                  // V^0 row x
+    tail[R1 + k] = (float)m->V[0][m->r[0] + k];   // V^0 row t
+  }
+  tail[2 * R1] = (float)m->U[L][0];
+  tail[2 * R1 + 1] = (float)m->b[L][0];
+  if (m->fast_pack) cudaFree(m->fast_pack);
+  if (m->rows_dev) cudaFree(m->rows_dev);
+  m->fast_pack = nullptr;
+  m->rows_dev = nullptr;
+  CK(cudaMalloc(&m->fast_pack, pk.size() * sizeof(float)));
+  CK(cudaMemcpy(m->fast_pack, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&m->rows_dev, rw.size() * sizeof(int32_t)));
+  CK(cudaMemcpy(m->rows_dev, rw.data(), rw.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  m->fRM = RMp;
+  m->fRH = RHp;
+  m->fast_dirty = false;
+  return LRNR_OK;
+}
+
+lrnr_status check_batch(const lrnr_model *m, const lrnr_batch *bt) {
+  if (!bt || bt->n_inst < 1 || bt->n_int < 0 || bt->n_ic < 0 || bt->n_bc < 0) return LRNR_EINVAL;
+  if (!bt->beta || !bt->nu || !bt->rho || !bt->int_off || !bt->ic_off || !bt->bc_off)
+    return LRNR_EINVAL;
+  if (bt->n_int > 0 && (!bt->x_int || !bt->t_int)) return LRNR_EINVAL;
+  if (bt->n_ic > 0 && !bt->x_ic) return LRNR_EINVAL;
+  if (bt->n_bc > 0 && !bt->t_bc) return LRNR_EINVAL;
+  (void)m;
+  return LRNR_OK;
+}
+
+// Common set-up of a residual / gradient pass.
+struct Pass {
+  KParams p;
+  int grid_cap;
+  int nb_entries;     // partial entries beyond dL/ds (dL/db block)
+};
+
+lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lrnr_batch *bt,
+                    bool grad, const float *s, cudaStream_t st, Pass &ps) {
+  lrnr_status rc = check_batch(m, bt);
+  if (rc != LRNR_OK) return rc;
+  if (!s) return LRNR_EINVAL;
+  KParams &p = ps.p;
+  std::memset(&p, 0, sizeof(p));
+  p.L = m->L;
+  p.M = m->M;
+  p.n_inst = bt->n_inst;
+  for (int l = 0; l <= m->L; ++l) p.r[l] = m->r[l];
+  for (int l = 0; l <= m->L + 1; ++l) p.roff[l] = m->roff[l];
+  p.sum_r = m->sum_r;
+  p.beta = bt->beta; p.nu = bt->nu; p.rho = bt->rho; p.s = s;
+  p.int_off = bt->int_off; p.ic_off = bt->ic_off; p.bc_off = bt->bc_off;
+  p.x_int = bt->x_int; p.t_int = bt->t_int; p.x_ic = bt->x_ic; p.t_bc = bt->t_bc;
+  p.grad = grad ? 1 : 0;
+  p.status = m->status_dev;
+  if (form == LRNR_FAST) {
+    if (prec != LRNR_FP32) return LRNR_ENOTSUP;
+    rc = build_fast_pack(m);
+    if (rc != LRNR_OK) return rc;
+    p.RM = m->fRM;
+    p.RH = m->fRH;
+    p.pack = m->fast_pack;
+    // 128 points per tile unless the per-point layer store would not fit
+    p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
+    if (!p.nt) return LRNR_ENOTSUP;
+    ps.nb_entries = m->L * p.RH + 1;
+  } else if (form == LRNR_FULL) {
+    p.RM = m->RM;
+    p.RH = 0;
+    if (prec == LRNR_FP32) {
+      p.pack = m->full_pack;
+      p.nt = full_fp32_choose_nt(m->L, p.RM, partial_len(m->L, p.RM, m->L * m->M + 1));
+      if (!p.nt) return LRNR_ENOTSUP;
+    } else if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
+      if (!m->tc_pack || !full_tc_supported(m->L, m->M, m->RM)) return LRNR_ENOTSUP;
+      p.pack = nullptr;
+      p.nt = full_tc_nt();
+    } else {
+      return LRNR_ENOTSUP;
+    }
+    ps.nb_entries = m->L * m->M + 1;
+  } else {
+    return LRNR_EINVAL;
+  }
+  p.P = grad ? partial_len(m->L, p.RM, ps.nb_entries - 1) : 0;
+  const int64_t tiles = max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, p.nt);
+  if (tiles > INT32_MAX / 2) return LRNR_EINVAL;
+  const size_t need = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1)) +
+                      (grad ? (size_t)tiles * p.P * sizeof(float) : 0);
+  rc = ensure_ws(m, need, st);
+  if (rc != LRNR_OK) return rc;
+  p.tile_off = reinterpret_cast<int32_t *>(m->ws);
+  p.partial = reinterpret_cast<float *>(static_cast<char *>(m->ws) +
+                                        align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1)));
+  p.loss = LRNR_LOSS_MSE;
+  p.w[0] = p.w[1] = p.w[2] = 1.0f;
+  ps.grid_cap = (int)std::min<int64_t>(tiles, INT32_MAX);
+  return LRNR_OK;
+}
+
+lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &ps,
+                     cudaStream_t st) {
+  KParams &p = ps.p;
+  CK(launch_tile_offsets(p, const_cast<int32_t *>(p.tile_off), st));
+  if (form == LRNR_FAST) {
+    CK(launch_fast(p, ps.grid_cap, st));
+  } else if (prec == LRNR_FP32) {
+    CK(launch_full_fp32(p, ps.grid_cap, st));
+  } else {
+    CK(launch_full_tc(p, m->tc_pack, (int)prec, ps.grid_cap, st));
+  }
+  return LRNR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lrnr_status_string(lrnr_status s) {
+  switch (s) {
+    case LRNR_OK: return "ok";
+    case LRNR_EINVAL: return "invalid argument";
+    case LRNR_ENOMEM: return "device allocation failed";
+    case LRNR_ECUDA: return "CUDA error";
+    case LRNR_ESINGULAR: return "singular interpolation block P^T Xi";
+    case LRNR_EEARLYSTOP: return "EIM stopped early";
+    case LRNR_ETIMEOUT: return "device wait reached its iteration cap";
+    case LRNR_ENOTREADY: return "not ready (FastLRNR layers not selected, or workspace too small while capturing)";
+    case LRNR_ENONFINITE: return "non-finite value met by a kernel";
+    case LRNR_ENOTSUP: return "form / precision not supported for this model";
+  }
+  return "unknown status";
+}
+
+lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U, const double *const *V,
+                       const double *const *b, lrnr_model **out) {
+  if (!out) return LRNR_EINVAL;
+  *out = nullptr;
+  if (L < 1 || L > LMAX || M < 1 || M > 4096 || !r || !U || !V || !b) return LRNR_EINVAL;
+  if (r[0] < 1 || r[0] > R1 || r[L] != 1) return LRNR_EINVAL;
+  for (int l = 1; l < L; ++l)
+    if (r[l] < 1 || r[l] > RMAX) return LRNR_EINVAL;
+  for (int l = 0; l <= L; ++l)
+    if (!U[l] || !V[l] || !b[l]) return LRNR_EINVAL;
+  lrnr_model *m = new (std::nothrow) lrnr_model();
+  if (!m) return LRNR_ENOMEM;
+  cudaGetDevice(&m->device);
+  cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  m->L = L;
+  m->M = M;
+  int rmid = 1;
+  for (int l = 0; l <= L; ++l) {
+    m->r[l] = r[l];
+    m->roff[l + 1] = m->roff[l] + r[l];
+    if (l > 0 && l < L) rmid = std::max(rmid, r[l]);
+  }
+  m->sum_r = m->roff[L + 1];
+  m->sum_m = L * M + 1;
+  m->RM = pad_rank(rmid);
+  m->U.resize(L + 1);
+  m->V.resize(L + 1);
+  m->b.resize(L + 1);
+  m->Uh.resize(L);
+  m->bh.resize(L);
+  m->Vh.resize(L);
+  m->rows.resize(L);
+  auto width = [&](int l) { return l < 0 ? 2 : (l < L ? M : 1); };
+  for (int l = 0; l <= L; ++l) {
+    const int mo = width(l), mi = width(l - 1);
+    m->U[l].assign(U[l], U[l] + (size_t)mo * r[l]);
+    m->V[l].assign(V[l], V[l] + (size_t)mi * r[l]);
+    m->b[l].assign(b[l], b[l] + mo);
+    for (double v : m->U[l]) if (!std::isfinite(v)) { delete m; return LRNR_EINVAL; }
+    for (double v : m->V[l]) if (!std::isfinite(v)) { delete m; return LRNR_EINVAL; }
+    for (double v : m->b[l]) if (!std::isfinite(v)) { delete m; return LRNR_EINVAL; }
+  }
+  // FP32 full pack
+  const int RM = m->RM;
+  const int64_t LS = full_layer_floats(M, RM);
+  std::vector<float> pk((size_t)full_pack_floats(L, M, RM), 0.0f);
+  for (int l = 0; l < L; ++l) {
+    float *Ul = pk.data() + l * LS, *bl = Ul + (size_t)M * RM, *Vn = bl + pad4(M);
+    const int rin = r[l], rout = r[l + 1];
+    for (int i = 0; i < M; ++i) {
+      for (int k = 0; k < rin; ++k) Ul[(size_t)i * RM + k] = (float)m->U[l][(size_t)i * rin + k];
+      bl[i] = (float)m->b[l][i];
+      for (int k = 0; k < rout; ++k) Vn[(size_t)i * RM + k] = (float)m->V[l + 1][(size_t)i * rout + k];
+    }
+  }
+  float *tail = pk.data() + L * LS;
+  for (int k = 0; k < r[0]; ++k) {
+    tail[k] = (float)m->V[0][k];
+    tail[R1 + k] = (float)m->V[0][r[0] + k];
+  }
+  tail[2 * R1] = (float)m->U[L][0];
+  tail[2 * R1 + 1] = (float)m->b[L][0];
+  // FP64 bases for snapshots
+  std::vector<double> w64;
+  std::vector<int64_t> offs;
+  for (int l = 0; l <= L; ++l) {
+    offs.push_back((int64_t)w64.size());
+    w64.insert(w64.end(), m->U[l].begin(), m->U[l].end());
+    offs.push_back((int64_t)w64.size());
+    w64.insert(w64.end(), m->V[l].begin(), m->V[l].end());
+    offs.push_back((int64_t)w64.size());
+    w64.insert(w64.end(), m->b[l].begin(), m->b[l].end());
+  }
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](cudaError_t err) {
+    lrnr_destroy(m);
+    return cuda_status(err);
+  };
+  if ((e = cudaMalloc(&m->full_pack, pk.size() * sizeof(float))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(m->full_pack, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&m->w64, w64.size() * sizeof(double))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(m->w64, w64.data(), w64.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&m->r_dev, sizeof(int) * (L + 1))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(m->r_dev, m->r, sizeof(int) * (L + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&m->offs_dev, sizeof(int64_t) * offs.size())) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(m->offs_dev, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&m->status_dev, sizeof(int))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemset(m->status_dev, 0, sizeof(int))) != cudaSuccess) return fail(e);
+  if (full_tc_supported(L, M, RM)) {
+    std::vector<unsigned char> tp;
+    full_tc_pack(L, M, RM, m->U, m->V, m->b, m->r, tp);
+    if ((e = cudaMalloc(&m->tc_pack, tp.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(m->tc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  }
+  *out = m;
+  return LRNR_OK;
+}
+
+lrnr_status lrnr_snapshots(lrnr_model *m, int layer, int64_t n_pts, const double *x,
+                           const double *t, int n_s, const double *s, double *out,
+                           void *stream) {
+  if (!m || layer < 0 || layer >= m->L || n_pts < 0 || n_s < 0) return LRNR_EINVAL;
+  if (n_pts * (int64_t)n_s == 0) return LRNR_OK;
+  if (!x || !t || !s || !out) return LRNR_EINVAL;
+  if (n_pts * (int64_t)n_s > INT32_MAX) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  CK(launch_snapshots_f64(m->w64, m->L, m->M, m->r_dev, m->offs_dev, layer, n_pts, x, t, n_s, s,
+                          m->sum_r, out, static_cast<cudaStream_t>(stream)));
+  return LRNR_OK;
+}
+
+lrnr_status fastlrnr_select_rows(lrnr_model *m, int layer, const double *snapshots, int64_t K,
+                                 int rhat, double tol, const int32_t *rows_in,
+                                 const double *Xi_in, int32_t *rows_out, double *Xi_out,
+                                 int *rhat_used, void *stream) {
+  if (!m || layer < 0 || layer >= m->L || rhat < 1 || rhat > RHMAX || rhat > m->M) return LRNR_EINVAL;
+  if (!(tol >= 0.0)) return LRNR_EINVAL;
+  if (!rows_in && (!snapshots || K < 1)) return LRNR_EINVAL;
+  if (rows_in && !Xi_in) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int M = m->M;
+  int32_t *rows_d = nullptr;
+  double *Xi_d = nullptr, *R = nullptr, *colmax = nullptr, *outb = nullptr;
+  int *est = nullptr;
+  lrnr_status rc = LRNR_OK;
+  int used = rhat;
+  const int rin = m->r[layer], rout = m->r[layer + 1];
+  std::vector<double> hb((size_t)rhat * (rin + 1 + rout));
+  std::vector<int32_t> hrows(rhat);
+  auto cleanup = [&]() {
+    if (rows_d) cudaFree(rows_d);
+    if (Xi_d) cudaFree(Xi_d);
+    if (R) cudaFree(R);
+    if (colmax) cudaFree(colmax);
+    if (outb) cudaFree(outb);
+    if (est) cudaFree(est);
+  };
+#define CKC(call)                            \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) {                 \
+      rc = cuda_status(e_);                  \
+      cleanup();                             \
+      return rc;                             \
+    }                                        \
+  } while (0)
+  CKC(cudaMalloc(&rows_d, sizeof(int32_t) * rhat));
+  CKC(cudaMalloc(&Xi_d, sizeof(double) * (size_t)M * rhat));
+  CKC(cudaMalloc(&outb, sizeof(double) * hb.size()));
+  CKC(cudaMemsetAsync(m->status_dev, 0, sizeof(int), st));
+  if (!rows_in) {
+    CKC(cudaMalloc(&R, sizeof(double) * (size_t)M * K));
+    CKC(cudaMalloc(&colmax, sizeof(double) * (size_t)K));
+    CKC(cudaMalloc(&est, sizeof(int) * 2));
+    CKC(cudaMemcpyAsync(R, snapshots, sizeof(double) * (size_t)M * K, cudaMemcpyDeviceToDevice, st));
+    CKC(launch_eim_greedy(R, M, K, rhat, tol, rows_d, Xi_d, est, colmax, nullptr, m->status_dev, st));
+    int hst[2];
+    CKC(cudaMemcpyAsync(hst, est, sizeof(hst), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    used = hst[0] ? hst[1] : rhat;
+  } else {
+    CKC(cudaMemcpyAsync(rows_d, rows_in, sizeof(int32_t) * rhat, cudaMemcpyDeviceToDevice, st));
+    CKC(cudaMemcpyAsync(Xi_d, Xi_in, sizeof(double) * (size_t)M * rhat, cudaMemcpyDeviceToDevice, st));
+  }
+  int dst = 0;
+  CKC(cudaMemcpyAsync(&dst, m->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKC(cudaStreamSynchronize(st));
+  if (dst == DEV_NONFINITE) { cleanup(); return LRNR_ENONFINITE; }
+  if (used < 1) { cleanup(); if (rhat_used) *rhat_used = 0; return LRNR_ESINGULAR; }
+  CKC(cudaMemcpy(hrows.data(), rows_d, sizeof(int32_t) * used, cudaMemcpyDeviceToHost));
+  {
+    std::vector<char> seen(M, 0);
+    for (int a = 0; a < used; ++a) {
+      if (hrows[a] < 0 || hrows[a] >= M || seen[hrows[a]]) { cleanup(); return LRNR_EINVAL; }
+      seen[hrows[a]] = 1;
+    }
+  }
+  const double *Ul = m->w64;  // offsets below
+  int64_t offs[3];
+  CKC(cudaMemcpy(offs, m->offs_dev + 3 * layer, sizeof(offs), cudaMemcpyDeviceToHost));
+  int64_t offn[3];
+  CKC(cudaMemcpy(offn, m->offs_dev + 3 * (layer + 1), sizeof(offn), cudaMemcpyDeviceToHost));
+  CKC(launch_eim_reduce_f64(Xi_d, rows_d, used, M, Ul + offs[0], Ul + offs[2], Ul + offn[1], rin,
+                            rout, outb, m->status_dev, st));
+  CKC(cudaMemcpyAsync(&dst, m->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKC(cudaStreamSynchronize(st));
+  if (dst == DEV_SINGULAR) { cleanup(); return LRNR_ESINGULAR; }
+  const size_t nb = (size_t)used * (rin + 1 + rout);
+  CKC(cudaMemcpy(hb.data(), outb, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+  for (double v : std::vector<double>(hb.begin(), hb.begin() + nb))
+    if (!std::isfinite(v)) { cleanup(); return LRNR_ESINGULAR; }
+  m->Uh[layer].assign(hb.begin(), hb.begin() + (size_t)used * rin);
+  m->bh[layer].assign(hb.begin() + (size_t)used * rin, hb.begin() + (size_t)used * (rin + 1));
+  m->Vh[layer].assign(hb.begin() + (size_t)used * (rin + 1), hb.begin() + nb);
+  m->rows[layer].assign(hrows.begin(), hrows.begin() + used);
+  m->rhat[layer] = used;
+  m->fast_dirty = true;
+  if (rows_out) CKC(cudaMemcpyAsync(rows_out, rows_d, sizeof(int32_t) * used, cudaMemcpyDeviceToDevice, st));
+  if (Xi_out) CKC(cudaMemcpyAsync(Xi_out, Xi_d, sizeof(double) * (size_t)M * used, cudaMemcpyDeviceToDevice, st));
+  CKC(cudaStreamSynchronize(st));
+  if (rhat_used) *rhat_used = used;
+  cleanup();
+#undef CKC
+  return LRNR_OK;
+}
+
+lrnr_status lrnr_residual(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lrnr_batch *bt,
+                          float *u, float *u_t, float *u_x, float *u_xx, float *res, float *res_ic,
+                          float *res_bc, void *stream) {
+  if (!m) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Pass ps;
+  lrnr_status rc = prepare(m, form, prec, bt, false, bt ? bt->s : nullptr, st, ps);
+  if (rc != LRNR_OK) return rc;
+  ps.p.u = u; ps.p.ut = u_t; ps.p.ux = u_x; ps.p.uxx = u_xx; ps.p.res = res;
+  ps.p.res_ic = res_ic; ps.p.res_bc = res_bc;
+  return run_main(m, form, prec, ps, st);
+}
+
+lrnr_status lrnr_residual_grad(lrnr_model *m, lrnr_form form, lrnr_precision prec,
+                               const lrnr_batch *bt, lrnr_loss loss, const float *w,
+                               float *loss_out, float *dL_ds, float *dL_db, void *stream) {
+  if (!m || !loss_out || !dL_ds) return LRNR_EINVAL;
+  if (loss != LRNR_LOSS_MSE && loss != LRNR_LOSS_L1) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Pass ps;
+  lrnr_status rc = prepare(m, form, prec, bt, true, bt ? bt->s : nullptr, st, ps);
+  if (rc != LRNR_OK) return rc;
+  ps.p.loss = loss;
+  if (w) { ps.p.w[0] = w[0]; ps.p.w[1] = w[1]; ps.p.w[2] = w[2]; }
+  rc = run_main(m, form, prec, ps, st);
+  if (rc != LRNR_OK) return rc;
+  if (dL_db) CK(cudaMemsetAsync(dL_db, 0, sizeof(float) * (size_t)bt->n_inst * m->sum_m, st));
+  const int DB0 = partial_db0(m->L, ps.p.RM);
+  const int n_needed = dL_db ? ps.p.P : DB0;
+  CK(launch_reduce(ps.p, n_needed, form == LRNR_FAST, m->rows_dev, ps.p.RH, loss_out, dL_ds,
+                   dL_db, m->sum_m, st));
+  return LRNR_OK;
+}
+
+lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lrnr_batch *bt,
+                          lrnr_loss loss, const float *w, float *s_inout, float *adam_m,
+                          float *adam_v, int64_t *step, int n_steps, float lr, float beta1,
+                          float beta2, float eps, float lambda_loc, const float *s_anchor,
+                          float *loss_out, void *stream) {
+  if (!m || !s_inout || !adam_m || !adam_v || !step || n_steps < 0) return LRNR_EINVAL;
+  if (loss != LRNR_LOSS_MSE && loss != LRNR_LOSS_L1) return LRNR_EINVAL;
+  if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f) || !(lambda_loc >= 0.0f))
+    return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Pass ps;
+  lrnr_status rc = prepare(m, form, prec, bt, true, s_inout, st, ps);
+  if (rc != LRNR_OK) return rc;
+  ps.p.loss = loss;
+  if (w) { ps.p.w[0] = w[0]; ps.p.w[1] = w[1]; ps.p.w[2] = w[2]; }
+  ps.p.step = step;
+  for (int k = 0; k < n_steps; ++k) {
+    rc = run_main(m, form, prec, ps, st);
+    if (rc != LRNR_OK) return rc;
+    CK(launch_reduce_adam(ps.p, s_inout, adam_m, adam_v, step, lr, beta1, beta2, eps, lambda_loc,
+                          s_anchor, loss_out, st));
+  }
+  return LRNR_OK;
+}
+
+lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
+  if (!m || max_points < 0 || max_inst < 1) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  const int nt_min = 32;
+  const int64_t tiles = max_points / nt_min + 3 * (int64_t)max_inst + 3;
+  int Pmax = partial_len(m->L, m->RM, m->L * m->M + 1);
+  Pmax = std::max(Pmax, partial_len(m->L, RMAX, m->L * RHMAX + 1));
+  const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) + (size_t)tiles * Pmax * sizeof(float);
+  return ensure_ws(m, need, nullptr);
+}
+
+lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int *sum_m,
+                            int *fast_ready) {
+  if (!m) return LRNR_EINVAL;
+  if (L) *L = m->L;
+  if (M) *M = m->M;
+  if (sum_r) *sum_r = m->sum_r;
+  if (sum_m) *sum_m = m->sum_m;
+  if (fast_ready) {
+    int ok = 1;
+    for (int l = 0; l < m->L; ++l) ok &= m->rhat[l] > 0;
+    *fast_ready = ok;
+  }
+  return LRNR_OK;
+}
+
+lrnr_status lrnr_last_device_status(lrnr_model *m) {
+  if (!m) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  CK(cudaDeviceSynchronize());
+  int v = 0;
+  CK(cudaMemcpy(&v, m->status_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(m->status_dev, 0, sizeof(int)));
+  switch (v) {
+    case DEV_OK: return LRNR_OK;
+    case DEV_NONFINITE: return LRNR_ENONFINITE;
+    case DEV_TIMEOUT: return LRNR_ETIMEOUT;
+    case DEV_SINGULAR: return LRNR_ESINGULAR;
+  }
+  return LRNR_ECUDA;
+}
+
+void lrnr_destroy(lrnr_model *m) {
+  if (!m) return;
+  DeviceGuard g(m->device);
+  cudaFree(m->full_pack);
+  cudaFree(m->w64);
+  cudaFree(m->r_dev);
+  cudaFree(m->offs_dev);
+  cudaFree(m->tc_pack);
+  cudaFree(m->fast_pack);
+  cudaFree(m->rows_dev);
+  cudaFree(m->status_dev);
+  cudaFree(m->ws);
+  delete m;
+}
+
+}  // extern "C"

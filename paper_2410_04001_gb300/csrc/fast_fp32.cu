@@ -1,0 +1,28 @@
+// FastLRNR residual + adjoint, FP32 SIMT: tile-size choice and dispatch over the
+// compiled (RM, RH) instantiations (each lives in its own translation unit).
+#include "fast_kernel.cuh"
+
+namespace lrnr {
+
+extern template cudaError_t launch_fast_t<8, 16>(const KParams &, int, cudaStream_t);
+extern template cudaError_t launch_fast_t<16, 16>(const KParams &, int, cudaStream_t);
+
+size_t fast_smem_bytes(int L, int RM, int RH, int NT, int P) {
+  return (size_t)FastLayout(L, RM, RH, NT, P).total * sizeof(float);
+}
+
+int fast_choose_nt(int L, int RM, int RH, int P) {
+  for (int nt : {128, 64, 32}) {
+    if (fast_smem_bytes(L, RM, RH, nt, P) <= (size_t)kSmemBudget) return nt;
+  }
+  return 0;
+}
+
+cudaError_t launch_fast(const KParams &p, int grid_cap, cudaStream_t st) {
+  if (p.nt != 128 && p.nt != 64 && p.nt != 32) return cudaErrorInvalidValue;
+  if (p.RM == 8 && p.RH == 16) return launch_fast_t<8, 16>(p, grid_cap, st);
+  if (p.RM == 16 && p.RH == 16) return launch_fast_t<16, 16>(p, grid_cap, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lrnr

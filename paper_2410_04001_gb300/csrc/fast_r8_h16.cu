@@ -1,0 +1,6 @@
+// FastLRNR FP32 kernel instantiated for padded rank 8 and 16 EIM rows.
+#include "fast_kernel.cuh"
+
+namespace lrnr {
+template cudaError_t launch_fast_t<8, 16>(const KParams &, int, cudaStream_t);
+}  // namespace lrnr

@@ -1,0 +1,181 @@
+// Internal declarations shared by the CUDA translation units of liblrnr.so.
+//
+// Work decomposition.  Collocation points are cut into tiles of NT points that
+// never straddle an instance or a point class (interior, initial, periodic pair);
+// tile_off[i] is the first tile of instance i.  A persistent grid walks the tile
+// list; each tile leaves one row of partial sums (loss, dL/ds, dL/db) in the
+// workspace, and a second kernel adds an instance's rows in tile order, so the
+// result does not depend on scheduling.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lrnr.h"
+
+namespace lrnr {
+
+constexpr int LMAX = 16;      // hidden layers supported
+constexpr int R1 = 2;         // padded rank of the input layer (input is (x, t))
+constexpr int RMAX = 32;      // largest hidden rank
+constexpr int RHMAX = 32;     // largest EIM row count per layer
+constexpr float TWO_PI_F = 6.28318530717958647692f;
+
+enum PointKind { KIND_INT = 0, KIND_IC = 1, KIND_BC = 2 };
+
+// Error codes the kernels write into the device status word (first writer wins).
+enum DevStatus { DEV_OK = 0, DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_SINGULAR = 3 };
+
+struct KParams {
+  int L, M, n_inst;
+  int RM;                      // padded hidden rank used by the packs
+  int RH;                      // padded EIM row count (fast form)
+  int r[LMAX + 1];             // ranks of the L+1 weight layers
+  int roff[LMAX + 2];          // offsets of each layer's s in an instance vector
+  int sum_r;
+  // batch (device)
+  const float *beta, *nu, *rho, *s;
+  const int64_t *int_off, *ic_off, *bc_off;
+  const float *x_int, *t_int, *x_ic, *t_bc;
+  // schedule
+  const int32_t *tile_off;     // [n_inst+1]
+  int nt;                      // points per tile (pairs per periodic tile: nt/2)
+  // packed weights (device)
+  const float *pack;
+  // gradient mode
+  int grad;
+  float *partial;              // [n_tiles][P]
+  int P;
+  int loss;                    // lrnr_loss
+  float w[3];
+  // evaluation mode outputs (any may be null)
+  float *u, *ut, *ux, *uxx, *res, *res_ic, *res_bc;
+  int64_t *step;               // spinprop: incremented once by block 0
+  int *status;
+};
+
+// --- layout of the FP32 packs -------------------------------------------------
+// Fast pack: per hidden layer l: Uh [RH][RM], bh [RH], Vh [RH][RM]; then V^0 [2][R1],
+// then U^L (scalar), b^L (scalar).  Unused (padded) entries are zero.
+__host__ __device__ inline int fast_layer_floats(int RM, int RH) { return RH * RM * 2 + RH; }
+__host__ __device__ inline int fast_pack_floats(int L, int RM, int RH) {
+  return L * fast_layer_floats(RM, RH) + 2 * R1 + 2;
+}
+// Full pack: per hidden layer l: U^l [M][RM], b^l [pad4(M)], V^{l+1} [M][RM]; then
+// V^0 [2][R1], U^L, b^L.  Every row starts on a 16-byte boundary.
+__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline int64_t full_layer_floats(int M, int RM) {
+  return (int64_t)M * RM * 2 + pad4(M);
+}
+__host__ __device__ inline int64_t full_pack_floats(int L, int M, int RM) {
+  return (int64_t)L * full_layer_floats(M, RM) + 2 * R1 + 2;
+}
+
+// Partial-sum row layout: [0] loss, [1 + l*RM + k] dL/ds (l = 0..L), then dL/db:
+// fast: [DB0 + l*RH + i] (hidden layers) and [DB0 + L*RH] (output bias);
+// full: [DB0 + l*M + i] and [DB0 + L*M].
+__host__ __device__ inline int partial_db0(int L, int RM) { return 1 + (L + 1) * RM; }
+__host__ __device__ inline int partial_len(int L, int RM, int nb) { return partial_db0(L, RM) + nb + 1; }
+
+// --- device helpers ----------------------------------------------------------
+__device__ __forceinline__ void set_status(int *status, int code) {
+  if (status) atomicCAS(status, DEV_OK, code);
+}
+
+struct Tile {
+  int inst, kind;
+  int64_t first;   // first point (interior / initial) or first pair (periodic)
+  int count;       // points (or pairs) in this tile
+};
+
+__device__ __forceinline__ Tile decode_tile(const KParams &p, int tile) {
+  // largest i with tile_off[i] <= tile
+  int lo = 0, hi = p.n_inst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(p.tile_off + mid) <= tile) lo = mid; else hi = mid - 1;
+  }
+  Tile t;
+  t.inst = lo;
+  int j = tile - __ldg(p.tile_off + lo);
+  int64_t a = __ldg(p.int_off + lo), nI = __ldg(p.int_off + lo + 1) - a;
+  int ntI = (int)((nI + p.nt - 1) / p.nt);
+  if (j < ntI) {
+    t.kind = KIND_INT; t.first = a + (int64_t)j * p.nt;
+    t.count = (int)(nI - (int64_t)j * p.nt < p.nt ? nI - (int64_t)j * p.nt : p.nt);
+    return t;
+  }
+  j -= ntI;
+  int64_t c = __ldg(p.ic_off + lo), nC = __ldg(p.ic_off + lo + 1) - c;
+  int ntC = (int)((nC + p.nt - 1) / p.nt);
+  if (j < ntC) {
+    t.kind = KIND_IC; t.first = c + (int64_t)j * p.nt;
+    t.count = (int)(nC - (int64_t)j * p.nt < p.nt ? nC - (int64_t)j * p.nt : p.nt);
+    return t;
+  }
+  j -= ntC;
+  int half = p.nt / 2;
+  int64_t e = __ldg(p.bc_off + lo), nB = __ldg(p.bc_off + lo + 1) - e;
+  t.kind = KIND_BC; t.first = e + (int64_t)j * half;
+  t.count = (int)(nB - (int64_t)j * half < half ? nB - (int64_t)j * half : half);
+  return t;
+}
+
+// Sum N values (N a power of two, <= 32) over the 32 lanes of a warp by recursive
+// halving.  On return lane l holds the warp total of value index l / (32 / N).
+template <int N>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = N / 2, off = 16; h >= 1; h /= 2, off /= 2) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      float send = up ? v[i] : v[i + h];
+      float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  float r = v[0];
+#pragma unroll
+  for (int off = 16 / N; off >= 1; off /= 2) r += __shfl_xor_sync(0xffffffffu, r, off);
+  return r;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off >= 1; off /= 2) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// tanh jet: value, first, second, third derivative (tanhf, not an approximation).
+__device__ __forceinline__ void tanh_d(float a, float &z, float &d1, float &d2) {
+  z = tanhf(a);
+  d1 = 1.0f - z * z;
+  d2 = -2.0f * z * d1;
+}
+
+// --- host-side launchers (defined in the .cu files) --------------------------
+constexpr int kSmemBudget = 220 * 1024;   // dynamic shared memory a tile kernel may use
+
+size_t fast_smem_bytes(int L, int RM, int RH, int NT, int P);
+int fast_choose_nt(int L, int RM, int RH, int P);
+size_t full_fp32_smem_bytes(int L, int RM, int NT, int P);
+int full_fp32_choose_nt(int L, int RM, int P);
+cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_t st);
+// grid_cap bounds the persistent grid (never more CTAs than tiles).
+cudaError_t launch_fast(const KParams &p, int grid_cap, cudaStream_t st);
+cudaError_t launch_full_fp32(const KParams &p, int grid_cap, cudaStream_t st);
+cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int grid_cap,
+                           cudaStream_t st);
+cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,
+                          int rows_stride, float *loss_out, float *dL_ds, float *dL_db,
+                          int sum_m, cudaStream_t st);
+cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
+                               float lr, float b1, float b2, float eps, float lam,
+                               const float *anchor, float *loss_out, cudaStream_t st);
+cudaError_t launch_eim_greedy(double *R, int M, int64_t K, int rhat, double tol, int32_t *rows,
+                              double *Xi, int *used_dev, double *colmax, int64_t *colarg,
+                              int *status, cudaStream_t st);
+
+}  // namespace lrnr

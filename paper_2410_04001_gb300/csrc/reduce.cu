@@ -1,0 +1,224 @@
+// Tile schedule, fixed-order reduction of per-tile partial sums, and the fused
+// Adam step on s (Sec. 2.3 gradient assembly; Sec. 3.2 Eq. 3.7; Sec. 4 Adam).
+#include "lrnr_internal.cuh"
+
+namespace lrnr {
+namespace {
+
+__device__ __forceinline__ int32_t tiles_of(const int64_t *io, const int64_t *co, const int64_t *bo,
+                                            int i, int nt) {
+  const int64_t nI = io[i + 1] - io[i], nC = co[i + 1] - co[i], nB = bo[i + 1] - bo[i];
+  const int half = nt / 2;
+  return (int32_t)((nI + nt - 1) / nt + (nC + nt - 1) / nt + (nB + half - 1) / half);
+}
+
+// tile_off[i] = first tile of instance i (exclusive prefix sum); one block.
+__global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *io, const int64_t *co,
+                                                       const int64_t *bo, int n_inst, int nt,
+                                                       int32_t *tile_off, int *status) {
+  __shared__ int32_t sums[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (n_inst + 1023) / 1024;
+  const int b = tid * chunk, e = min(n_inst, b + chunk);
+  int32_t acc = 0;
+  for (int i = b; i < e; ++i) {
+    if (io[i + 1] < io[i] || co[i + 1] < co[i] || bo[i + 1] < bo[i]) set_status(status, DEV_NONFINITE);
+    acc += tiles_of(io, co, bo, i, nt);
+  }
+  sums[tid] = acc;
+  __syncthreads();
+  for (int off = 1; off < 1024; off *= 2) {
+    const int32_t v = tid >= off ? sums[tid - off] : 0;
+    __syncthreads();
+    sums[tid] += v;
+    __syncthreads();
+  }
+  int32_t run = sums[tid] - acc;
+  for (int i = b; i < e; ++i) {
+    tile_off[i] = run;
+    run += tiles_of(io, co, bo, i, nt);
+  }
+  if (tid == 1023) tile_off[n_inst] = sums[1023];
+}
+
+struct RedArgs {
+  const float *partial;
+  const int32_t *tile_off;
+  int P, n_needed;        // row length, leading entries to reduce
+  int L, M, RM, RH, fast;
+  int r[LMAX + 1], roff[LMAX + 2];
+  int sum_r, sum_m;
+  const int32_t *rows;    // fast: [L][RH], -1 = unused
+  float *loss_out, *dL_ds, *dL_db;
+};
+
+__device__ __forceinline__ void scatter_out(const RedArgs &a, int i, int j, float v) {
+  const int DB0 = 1 + (a.L + 1) * a.RM;
+  if (j == 0) {
+    if (a.loss_out) a.loss_out[i] = v;
+  } else if (j < DB0) {
+    const int l = (j - 1) / a.RM, k = (j - 1) % a.RM;
+    if (k < a.r[l]) a.dL_ds[(int64_t)i * a.sum_r + a.roff[l] + k] = v;
+  } else if (a.dL_db) {
+    const int jj = j - DB0;
+    float *db = a.dL_db + (int64_t)i * a.sum_m;
+    if (a.fast) {
+      if (jj == a.L * a.RH) db[a.L * a.M] = v;
+      else {
+        const int l = jj / a.RH, ii = jj % a.RH;
+        const int row = a.rows[l * a.RH + ii];
+        if (row >= 0) db[l * a.M + row] = v;
+      }
+    } else {
+      db[jj] = v;   // hidden layers l*M + i, then the output bias at L*M
+    }
+  }
+}
+
+// grid (n_inst, ceil(n_needed / 32)), block (32, 32): x = entry, y = tile group.
+__global__ void __launch_bounds__(1024) k_reduce(const __grid_constant__ RedArgs a) {
+  __shared__ float sh[32][33];
+  const int i = blockIdx.x;
+  const int j = blockIdx.y * 32 + threadIdx.x;
+  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
+  float acc = 0.0f;
+  if (j < a.n_needed)
+    for (int t = t0 + threadIdx.y; t < t1; t += 32) acc += a.partial[(int64_t)t * a.P + j];
+  sh[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < a.n_needed) {
+    float tot = 0.0f;
+#pragma unroll
+    for (int g = 0; g < 32; ++g) tot += sh[g][threadIdx.x];
+    scatter_out(a, i, j, tot);
+  }
+}
+
+struct AdamArgs {
+  RedArgs red;
+  float *s, *m, *v;
+  const int64_t *step;
+  float lr, b1, b2, eps, lam;
+  const float *anchor;
+};
+
+// One block per instance: reduce loss and dL/ds, add the locality subgradient,
+// then apply Adam to the instance's s.
+__global__ void __launch_bounds__(1024) k_reduce_adam(const __grid_constant__ AdamArgs A) {
+  const RedArgs &a = A.red;
+  __shared__ float sh[32][33];
+  __shared__ float gsh[(LMAX + 1) * RMAX];
+  __shared__ float lsum[32];
+  const int i = blockIdx.x;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
+  const int DB0 = 1 + (a.L + 1) * a.RM;
+  float loss = 0.0f;
+  for (int c0 = 0; c0 < DB0; c0 += 32) {
+    const int j = c0 + tx;
+    float acc = 0.0f;
+    if (j < DB0)
+      for (int t = t0 + ty; t < t1; t += 32) acc += a.partial[(int64_t)t * a.P + j];
+    sh[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && j < DB0) {
+      float tot = 0.0f;
+#pragma unroll
+      for (int g = 0; g < 32; ++g) tot += sh[g][tx];
+      if (j == 0) loss = tot;
+      else {
+        const int l = (j - 1) / a.RM, k = (j - 1) % a.RM;
+        if (k < a.r[l]) gsh[a.roff[l] + k] = tot;
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t k = *A.step;
+  const float bc1 = 1.0f - powf(A.b1, (float)k);
+  const float bc2 = 1.0f - powf(A.b2, (float)k);
+  float loc = 0.0f;
+  for (int q = tid; q < a.sum_r; q += 1024) {
+    const int64_t o = (int64_t)i * a.sum_r + q;
+    const float sv = A.s[o];
+    float g = gsh[q];
+    if (A.anchor) {
+      const float d = sv - A.anchor[o];
+      loc += A.lam * fabsf(d);
+      g += A.lam * (float)((d > 0.0f) - (d < 0.0f));
+    }
+    if (a.dL_ds) a.dL_ds[o] = g;
+    const float mv = A.b1 * A.m[o] + (1.0f - A.b1) * g;
+    const float vv = A.b2 * A.v[o] + (1.0f - A.b2) * g * g;
+    A.m[o] = mv;
+    A.v[o] = vv;
+    A.s[o] = sv - A.lr * (mv / bc1) / (sqrtf(vv / bc2) + A.eps);
+  }
+  loc = warp_sum(loc);
+  if (tx == 0) lsum[ty] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    float lt = 0.0f;
+    for (int w = 0; w < 32; ++w) lt += lsum[w];
+    if (a.loss_out) a.loss_out[i] = loss + lt;
+  }
+}
+
+void fill_red(RedArgs &a, const KParams &p, int n_needed, int fast, const int32_t *rows,
+              float *loss_out, float *dL_ds, float *dL_db, int sum_m) {
+  a.partial = p.partial;
+  a.tile_off = p.tile_off;
+  a.P = p.P;
+  a.n_needed = n_needed;
+  a.L = p.L;
+  a.M = p.M;
+  a.RM = p.RM;
+  a.RH = p.RH;
+  a.fast = fast;
+  for (int l = 0; l <= LMAX; ++l) a.r[l] = p.r[l];
+  for (int l = 0; l <= LMAX + 1; ++l) a.roff[l] = p.roff[l];
+  a.sum_r = p.sum_r;
+  a.sum_m = sum_m;
+  a.rows = rows;
+  a.loss_out = loss_out;
+  a.dL_ds = dL_ds;
+  a.dL_db = dL_db;
+}
+
+}  // namespace
+
+cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_t st) {
+  k_tile_offsets<<<1, 1024, 0, st>>>(p.int_off, p.ic_off, p.bc_off, p.n_inst, p.nt, tile_off,
+                                     p.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const KParams &p, int n_needed, int form_fast, const int32_t *rows,
+                          int /*rows_stride*/, float *loss_out, float *dL_ds, float *dL_db,
+                          int sum_m, cudaStream_t st) {
+  RedArgs a;
+  fill_red(a, p, n_needed, form_fast, rows, loss_out, dL_ds, dL_db, sum_m);
+  dim3 grid(p.n_inst, (n_needed + 31) / 32), block(32, 32);
+  k_reduce<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
+                               float lr, float b1, float b2, float eps, float lam,
+                               const float *anchor, float *loss_out, cudaStream_t st) {
+  AdamArgs A;
+  fill_red(A.red, p, 1 + (p.L + 1) * p.RM, 0, nullptr, loss_out, nullptr, nullptr, 0);
+  A.s = s;
+  A.m = m;
+  A.v = v;
+  A.step = step;
+  A.lr = lr;
+  A.b1 = b1;
+  A.b2 = b2;
+  A.eps = eps;
+  A.lam = lam;
+  A.anchor = anchor;
+  k_reduce_adam<<<p.n_inst, dim3(32, 32), 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace lrnr

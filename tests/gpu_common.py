@@ -1,0 +1,58 @@
+"""Helpers shared by the GPU parity tests: build the same seeded workload for the
+CUDA library and for the FP64 oracle, and compare them."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import synth
+from oracle import eim64, lrnr64
+
+TOL_FP32 = 1e-5     # normwise relative error of each quantity, FP32 path vs FP64 oracle
+
+
+def rel(a, b) -> float:
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    n = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / n) if n > 0 else float(np.linalg.norm(a - b))
+
+
+def as_f32_batch(bt):
+    """Round the batch to FP32 exactly as the device sees it, so both sides use the
+    same inputs."""
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    return synth.Batch(beta=f(bt.beta), nu=f(bt.nu), rho=f(bt.rho), s=f(bt.s),
+                       int_off=bt.int_off, ic_off=bt.ic_off, bc_off=bt.bc_off,
+                       x_int=f(bt.x_int), t_int=f(bt.t_int), x_ic=f(bt.x_ic), t_bc=f(bt.t_bc))
+
+
+def as_f32_net(net):
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    return synth.Net(L=net.L, M=net.M, r=net.r, U=[f(u) for u in net.U], V=[f(v) for v in net.V],
+                     b=[f(b) for b in net.b])
+
+
+def eim_for(net, s, rhat, n_per_point=8, seed=77, tol=0.0):
+    """Oracle EIM rows / bases of every hidden layer from the standard snapshot design."""
+    g = synth.rng(seed)
+    xs, ts = synth.snapshot_design(g, n_per_point)
+    rows, Xis, Ss = [], [], []
+    for l in range(net.L):
+        S = lrnr64.hidden_states(net, s, xs, ts, l)
+        p, Xi, _ = eim64.eim_greedy(S, rhat, tol)
+        rows.append(p)
+        Xis.append(Xi)
+        Ss.append(S)
+    return rows, Xis, Ss
+
+
+def install_fast(P, model, rows, Xis):
+    for l, (p, Xi) in enumerate(zip(rows, Xis)):
+        r_in = torch.tensor(np.asarray(p, np.int32), device="cuda")
+        X_in = torch.tensor(np.ascontiguousarray(Xi.T), device="cuda")
+        P.fastlrnr_select_rows(model, l, rhat=len(p), rows_in=r_in, Xi_in=X_in)
+
+
+def per_instance_rel(a, b):
+    return max(rel(a[i], b[i]) for i in range(b.shape[0]))
