@@ -1,0 +1,487 @@
+"""Benchmark of the FastLRNR / SPInProp hot path on one GB300 (or N replicas).
+
+Workload: the single-instance convection-diffusion-reaction problem
+(beta = 5, nu = 1, rho = 2) on an LRNR with L = 5 hidden layers of width M = 256
+and rank r = 16, FastLRNR with 16 EIM rows per layer; 65,536 interior points,
+2,048 initial points and 1,024 periodic pairs (69,632 collocation points).
+
+A step is one fused SPInProp pass through the C ABI (``spinprop_step``, one Adam
+step): input jets, reduced layers, output, CDR residual, loss and seeds, adjoint
+sweep, fixed-order gradient reduction and the Adam update of s.  The metric is
+collocation points per second.  The same run times the full-width FP32 LRNR
+residual + gradient on the same batch (``variants``) and measures the error of
+each path against the FP64 oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "residual+grad points/s, FastLRNR & full LRNR, BF16 vs FP32, err vs FP64 oracle"
+WORKLOAD = ("CDR beta=5 nu=1 rho=2; LRNR L=5 hidden layers, M=256, r=16, tanh; FastLRNR "
+            "rhat=16 rows/layer (EIM); 65,536 interior + 2,048 initial + 1,024 periodic pairs")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- peaks
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return GB300_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------- flops model
+
+def fast_flops_per_point(r, rhat, channels):
+    """Algorithmic FP32 flops of one point through the FastLRNR forward + adjoint
+    (no recomputation counted): per hidden layer 2*C*rh*(2*r_in + 2*r_out) for the
+    four reduced products, plus ~30 flops per row for the tanh jet and its adjoint."""
+    L = len(r) - 1
+    tot = 0
+    for l in range(L):
+        tot += 2 * channels * rhat[l] * (2 * r[l] + 2 * r[l + 1]) + 30 * rhat[l]
+    return tot
+
+
+def full_flops_per_point(r, M, channels):
+    L = len(r) - 1
+    tot = 0
+    for l in range(L):
+        tot += 2 * channels * M * (2 * r[l] + 2 * r[l + 1]) + 30 * M
+    return tot
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU baseline
+
+def cpu_baseline_child():
+    """Runs in a fresh interpreter: time the FP64 oracle's SPInProp step (FastLRNR
+    residual + gradient + Adam) on a bounded sample of the workload."""
+    import numpy as np
+    import synth
+    from oracle import adam64, eim64, lrnr64
+    net, bt = synth.workload_cdr_single()
+    g = synth.rng(77)
+    xs, ts = synth.snapshot_design(g, 8)
+    rows, Xis = [], []
+    for l in range(net.L):
+        p, Xi, _ = eim64.eim_greedy(lrnr64.hidden_states(net, bt.s[0], xs, ts, l), 16)
+        rows.append(p)
+        Xis.append(Xi)
+    fnet = lrnr64.make_fast(net, rows, Xis)
+    inst = bt.instance(0)
+    s = inst["s"].copy()
+    m = np.zeros_like(s)
+    v = np.zeros_like(s)
+    n_pts = bt.n_points
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        k += 1
+        _, gs, _ = lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet,
+                                             dict(inst, s=s))
+        s, m, v = adam64.adam_step(s, m, v, k, gs)
+        if time.perf_counter() - t0 > 12.0 or k >= 50:
+            break
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": n_pts * k / dt, "steps": k, "seconds": dt, "points": n_pts}))
+
+
+def run_cpu_baseline():
+    cores = len(os.sched_getaffinity(0))
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child"],
+                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if not line:
+        return {"value": None, "unit": "points/s", "cores": cores, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(line[-1])
+    return {"value": d["value"], "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, FastLRNR SPInProp step (residual + gradient + Adam) "
+                       f"over the full 69,632-point batch, {d['steps']} steps in {d['seconds']:.1f} s; "
+                       f"BLAS threads = {cores}")}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    import numpy as np
+    import synth
+    from oracle import adam64, eim64, lrnr64
+    net, bt = synth.workload_cdr_single()
+    g = synth.rng(77)
+    xs, ts = synth.snapshot_design(g, 8)
+    rows, Xis = [], []
+    for l in range(net.L):
+        p, Xi, _ = eim64.eim_greedy(lrnr64.hidden_states(net, bt.s[0], xs, ts, l), 16)
+        rows.append(p)
+        Xis.append(Xi)
+    fnet = lrnr64.make_fast(net, rows, Xis)
+    inst = bt.instance(0)
+    # each step: the oracle SPInProp step on a bounded sample (1/8 of the interior,
+    # initial and periodic points), so that K steps finish in a few minutes
+    sub = dict(inst)
+    sub["x_int"], sub["t_int"] = inst["x_int"][::8], inst["t_int"][::8]
+    sub["x_ic"], sub["t_bc"] = inst["x_ic"][::8], inst["t_bc"][::8]
+    n_pts = len(sub["x_int"]) + len(sub["x_ic"]) + 2 * len(sub["t_bc"])
+    s = inst["s"].copy()
+    m = np.zeros_like(s)
+    v = np.zeros_like(s)
+    k = 0
+
+    def step():
+        nonlocal s, m, v, k
+        k += 1
+        _, gs, _ = lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet, dict(sub, s=s))
+        s, m, v = adam64.adam_step(s, m, v, k, gs)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n_pts * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + "; FastLRNR SPInProp step on a 1/8 point sample", "form": "fast"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"every 8th point of each class ({n_pts} points per step)"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------- our arm
+
+def main():
+    if "--cpu-baseline-child" in sys.argv:
+        cpu_baseline_child()
+        return
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_oracle:
+        cpu_base = run_cpu_baseline()          # before the first GPU call
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_04001_gb300 as P
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    net, bt = synth.workload_cdr_single()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    dev = torch.device("cuda", local)
+    db = P.DeviceBatch.from_host(bt, dev)
+    # FastLRNR construction: exact-LRNR snapshots at the 4 x 3 design plus
+    # perturbations (device, FP64), EIM greedy on the device
+    g = synth.rng(77)
+    xs, ts = synth.snapshot_design(g, 8)
+    xs_d = torch.tensor(xs, device=dev)
+    ts_d = torch.tensor(ts, device=dev)
+    s0 = torch.tensor(bt.s[:1], device=dev)
+    rows_all = []
+    for l in range(net.L):
+        S = P.lrnr_snapshots(model, l, xs_d, ts_d, s0)
+        rows, _, used = P.fastlrnr_select_rows(model, l, S, 16)
+        rows_all.append(rows.cpu().numpy())
+    n_pts = db.n_points
+    P.lrnr_reserve(model, n_pts, 1)
+
+    s = db.s.clone()
+    m = torch.zeros_like(s)
+    v = torch.zeros_like(s)
+    step_ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    loss_out = torch.zeros(1, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def spin():
+        P.spinprop_step(model, "fast", "fp32", db, s, m, v, step_ctr, 1, lr=1e-3, loss_out=loss_out)
+
+    # CUDA graph of one step (3 kernels); kernel timing events are recorded inside it
+    P.lrnr_timing(model, True)
+    for _ in range(3):
+        spin()
+    torch.cuda.synchronize()
+    P.lrnr_timing_read(model)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        spin()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(fn, n, timing_model=None):
+        """Run n steps, flushing L2 (256 MiB write) before each; return per-step ms
+        (CUDA events on the launching stream) and the tile-kernel ms."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        kern = 0.0
+        kl = 0
+        for i in range(n):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+            if timing_model is not None:
+                ms, c = P.lrnr_timing_read(timing_model)
+                kern += ms
+                kl += c
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], kern, kl
+
+    for _ in range(args.warmup):
+        graph.replay()
+        P.lrnr_timing_read(model)
+    torch.cuda.synchronize()
+    P.lrnr_timing_read(model)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    per_step, kern_ms, kern_n = timed_steps(graph.replay, args.steps, model)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_step = sum(per_step) / len(per_step)
+    if dist:
+        tt = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    value = world * n_pts / (ms_step * 1e-3)
+
+    # ---- roofline of the dominant kernel (the fused FastLRNR kernel)
+    ch = 4
+    pf_int = fast_flops_per_point(net.r, [16] * net.L, ch)
+    pf_bnd = fast_flops_per_point(net.r, [16] * net.L, 1)
+    flops_launch = bt.x_int.shape[0] * pf_int + (bt.x_ic.shape[0] + 2 * bt.t_bc.shape[0]) * pf_bnd
+    k_avg_ms = kern_ms / max(1, kern_n)
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_max)
+    achieved = flops_launch / (k_avg_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_fast<16,16> (fused FastLRNR residual + adjoint)",
+            "kernel_ms": k_avg_ms, "flops_per_launch": flops_launch,
+            "peak_note": f"FP32 FMA peak = 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (max SM clock, {src} peaks file)"}
+
+    # ---- variants: full-width FP32 LRNR residual + gradient, fast residual + gradient
+    variants = {}
+    P.lrnr_timing(model, True)
+    for form, prec in (("full", "fp32"), ("fast", "fp32")):
+        out = P.lrnr_residual_grad(model, form, prec, db)
+        torch.cuda.synchronize()
+        P.lrnr_timing_read(model)
+        nrep = 5 if form == "full" else 50
+        ts_, km, kn = timed_steps(lambda: P.lrnr_residual_grad(model, form, prec, db, out=out), nrep, model)
+        step_ms = sum(ts_) / len(ts_)
+        kms = km / max(1, kn)
+        fl = (bt.x_int.shape[0] * (full_flops_per_point(net.r, net.M, 4) if form == "full" else pf_int)
+              + (bt.x_ic.shape[0] + 2 * bt.t_bc.shape[0]) *
+              (full_flops_per_point(net.r, net.M, 1) if form == "full" else pf_bnd))
+        variants[f"{form}_{prec}"] = {
+            "points_per_s": n_pts / (step_ms * 1e-3), "ms_per_call": step_ms, "kernel_ms": kms,
+            "tflops": fl / (kms * 1e-3) / 1e12, "frac_fp32_peak": fl / (kms * 1e-3) / 1e12 / peak,
+            "hbm_gbs": (n_pts * 8) / (kms * 1e-3) / 1e9}
+    P.lrnr_timing(model, False)
+
+    # ---- errors against the FP64 oracle (full batch, same inputs)
+    if rank == 0 and not args.no_oracle:
+        from oracle import lrnr64, eim64
+
+        def rel(a, b):
+            a = np.asarray(a, np.float64).ravel()
+            b = np.asarray(b, np.float64).ravel()
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        bt32 = synth.Batch(beta=f32(bt.beta), nu=f32(bt.nu), rho=f32(bt.rho), s=f32(bt.s),
+                           int_off=bt.int_off, ic_off=bt.ic_off, bc_off=bt.bc_off,
+                           x_int=f32(bt.x_int), t_int=f32(bt.t_int), x_ic=f32(bt.x_ic), t_bc=f32(bt.t_bc))
+        Xis = []
+        for l in range(net.L):
+            Sd = P.lrnr_snapshots(model, l, xs_d, ts_d, s0).cpu().numpy().T
+            p, Xi, _ = eim64.eim_greedy(Sd, 16)
+            assert np.array_equal(p, rows_all[l]), "EIM rows differ from the oracle"
+            Xis.append(Xi)
+        fnet = lrnr64.make_fast(net, rows_all, Xis)
+        for form, ref in (("fast", fnet), ("full", net)):
+            lo, ds, dbb = P.lrnr_residual_grad(model, form, "fp32", db)
+            ro, rs, rb = lrnr64.residual_grad(ref, bt32, form)
+            variants[f"{form}_fp32"]["err_vs_fp64_oracle"] = {
+                "loss": rel(lo.cpu(), ro), "dL_ds": rel(ds.cpu(), rs), "dL_db": rel(dbb.cpu(), rb)}
+        variants["fast_fp32"]["eim_rows_bit_exact"] = True
+
+    # ---- end to end: host buffers in, loss and s back, through the public API
+    host = {k: t.detach().cpu().pin_memory() for k, t in db.tensors.items()}
+    dev_in = {k: torch.empty_like(t) for k, t in db.tensors.items()}
+    db_e2e = P.DeviceBatch(db.n_inst, **dev_in)
+    s_host = s.detach().cpu().pin_memory()
+    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    s_back = torch.empty_like(s_host).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = loss_host.numel() * 4 + s_back.numel() * 4
+
+    def e2e_step():
+        for k, t in host.items():
+            dev_in[k].copy_(t, non_blocking=True)
+        s.copy_(s_host, non_blocking=True)
+        P.spinprop_step(model, "fast", "fp32", db_e2e, s, m, v, step_ctr, 1, lr=1e-3, loss_out=loss_out)
+        loss_host.copy_(loss_out, non_blocking=True)
+        s_back.copy_(s, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    e_ts, _, _ = timed_steps(e2e_step, max(20, args.steps // 4))
+    e2e_ms = sum(e_ts) / len(e_ts)
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    status = P.lrnr_last_device_status(model)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "FastLRNR SPInProp step (spinprop_step, 1 Adam step)",
+                       "points_per_step": n_pts, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed before every timed step (256 MiB write)", "cuda_graph": True},
+            "roofline": roof,
+            "cpu_baseline": cpu_base,
+            "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": "points/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "note": "pinned host -> device inputs and s, spinprop_step, loss and s back to host"},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "wall_s_timed_region": t_wall,
+            "device_status": status,
+            "variants": variants,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

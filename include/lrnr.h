@@ -189,6 +189,17 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst);
 lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int *sum_m,
                             int *fast_ready);
 
+/* lrnr_timing -- when enable != 0, record a CUDA event pair on the launch stream
+ * around every tile kernel (the fused residual / adjoint kernel) of later calls.
+ * Recording is captured by CUDA graphs like any stream work. */
+lrnr_status lrnr_timing(lrnr_model *m, int enable);
+
+/* lrnr_timing_read -- wait for the recorded events, return the summed kernel time
+ * (host, milliseconds) and the number of timed launches since the last read (or
+ * since lrnr_timing), and start a new count.  After a CUDA graph replay, read
+ * once per replay: the graph re-records the same events. */
+lrnr_status lrnr_timing_read(lrnr_model *m, double *ms_total, int64_t *launches);
+
 /* lrnr_last_device_status -- synchronises the device, returns and clears the
  * status word written by kernels (LRNR_OK if none). */
 lrnr_status lrnr_last_device_status(lrnr_model *m);

@@ -60,6 +60,8 @@ _SIGS = {
                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
     "lrnr_reserve": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "lrnr_model_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lrnr_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lrnr_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "lrnr_last_device_status": (ctypes.c_int, [_P]),
     "lrnr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lrnr_destroy": (None, [_P]),
@@ -160,6 +162,18 @@ def lrnr_model_info(model: Model) -> dict:
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib().lrnr_model_info(model.handle, *[ctypes.byref(x) for x in v]), "lrnr_model_info")
     return dict(zip(("L", "M", "sum_r", "sum_m", "fast_ready"), [x.value for x in v]))
+
+
+def lrnr_timing(model: Model, enable: bool = True):
+    _check(lib().lrnr_timing(model.handle, int(bool(enable))), "lrnr_timing")
+
+
+def lrnr_timing_read(model: Model):
+    """(summed tile-kernel milliseconds, launches) since the last read."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(lib().lrnr_timing_read(model.handle, ctypes.byref(ms), ctypes.byref(n)), "lrnr_timing_read")
+    return ms.value, n.value
 
 
 def lrnr_last_device_status(model: Model) -> int:

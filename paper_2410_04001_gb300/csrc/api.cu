@@ -53,6 +53,10 @@ struct lrnr_model {
   int *status_dev = nullptr;
   void *ws = nullptr;
   size_t ws_bytes = 0;
+  // optional CUDA-event timing of the tile kernels (one event pair per launch)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_start, ev_stop;
+  size_t ev_used = 0;
 };
 
 namespace {
@@ -245,6 +249,20 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
                      cudaStream_t st) {
   KParams &p = ps.p;
   CK(launch_tile_offsets(p, const_cast<int32_t *>(p.tile_off), st));
+  cudaEvent_t e1 = nullptr, e2 = nullptr;
+  if (m->timing) {
+    if (m->ev_used == m->ev_start.size()) {
+      cudaEvent_t a, b;
+      CK(cudaEventCreate(&a));
+      CK(cudaEventCreate(&b));
+      m->ev_start.push_back(a);
+      m->ev_stop.push_back(b);
+    }
+    e1 = m->ev_start[m->ev_used];
+    e2 = m->ev_stop[m->ev_used];
+    ++m->ev_used;
+    CK(cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+  }
   if (form == LRNR_FAST) {
     CK(launch_fast(p, ps.grid_cap, st));
   } else if (prec == LRNR_FP32) {
@@ -252,6 +270,7 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
   } else {
     CK(launch_full_tc(p, m->tc_pack, (int)prec, ps.grid_cap, st));
   }
+  if (e2) CK(cudaEventRecordWithFlags(e2, st, cudaEventRecordExternal));
   return LRNR_OK;
 }
 
@@ -571,6 +590,29 @@ lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int
   return LRNR_OK;
 }
 
+lrnr_status lrnr_timing(lrnr_model *m, int enable) {
+  if (!m) return LRNR_EINVAL;
+  m->timing = enable != 0;
+  m->ev_used = 0;
+  return LRNR_OK;
+}
+
+lrnr_status lrnr_timing_read(lrnr_model *m, double *ms_total, int64_t *launches) {
+  if (!m) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
+  double tot = 0.0;
+  for (size_t i = 0; i < m->ev_used; ++i) {
+    CK(cudaEventSynchronize(m->ev_stop[i]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, m->ev_start[i], m->ev_stop[i]));
+    tot += ms;
+  }
+  if (ms_total) *ms_total = tot;
+  if (launches) *launches = (int64_t)m->ev_used;
+  m->ev_used = 0;
+  return LRNR_OK;
+}
+
 lrnr_status lrnr_last_device_status(lrnr_model *m) {
   if (!m) return LRNR_EINVAL;
   DeviceGuard g(m->device);
@@ -599,6 +641,8 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->rows_dev);
   cudaFree(m->status_dev);
   cudaFree(m->ws);
+  for (auto e : m->ev_start) cudaEventDestroy(e);
+  for (auto e : m->ev_stop) cudaEventDestroy(e);
   delete m;
 }
 

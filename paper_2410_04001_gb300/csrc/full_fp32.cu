@@ -8,6 +8,7 @@
 // reverse sweep rebuilds each row's pre-activation from the stored rank-r input
 // (C x r floats per point per layer) instead of keeping M-wide activations.
 #include "lrnr_internal.cuh"
+#include "point_common.cuh"
 #include "simt_common.cuh"
 
 #include <algorithm>
@@ -120,28 +121,9 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
   const float *V0 = p.pack + L * LS;
   const float Uout = __ldg(V0 + 2 * R1);
   const float bout = __ldg(V0 + 2 * R1 + 1);
-  const int inst = T.inst;
 
-  bool act;
-  float x, t;
-  int side = 0;
-  if (T.kind == KIND_BC) {
-    const int pr = tid >> 1;
-    side = tid & 1;
-    act = pr < T.count;
-    t = act ? __ldg(p.t_bc + T.first + pr) : 0.5f;
-    x = side ? TWO_PI_F : 0.0f;
-  } else {
-    act = tid < T.count;
-    const int64_t g = T.first + tid;
-    if (T.kind == KIND_INT) {
-      x = act ? __ldg(p.x_int + g) : 1.0f;
-      t = act ? __ldg(p.t_int + g) : 0.5f;
-    } else {
-      x = act ? __ldg(p.x_ic + g) : 1.0f;
-      t = 0.0f;
-    }
-  }
+  const PointIn pt = load_point(p, T, tid);
+  const float x = pt.x, t = pt.t;
   float v00 = __ldg(V0 + 0), v01 = __ldg(V0 + 1), v10 = __ldg(V0 + R1), v11 = __ldg(V0 + R1 + 1);
 
   float q[C][RM];
@@ -185,58 +167,8 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
   for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0];
   u[0] += bout;
 
-  const float beta = __ldg(p.beta + inst), nu = __ldg(p.nu + inst), rho = __ldg(p.rho + inst);
-  float ub[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  float lp = 0.0f;
-  if (T.kind == KIND_INT) {
-    const float R = u[1] + beta * u[2] - nu * u[3] - rho * u[0] * (1.0f - u[0]);
-    if (!p.grad) {
-      if (act) {
-        const int64_t g = T.first + tid;
-        if (p.u) p.u[g] = u[0];
-        if (p.ut) p.ut[g] = u[1];
-        if (p.ux) p.ux[g] = u[2];
-        if (p.uxx) p.uxx[g] = u[3];
-        if (p.res) p.res[g] = R;
-      }
-      return;
-    }
-    const float n = (float)(__ldg(p.int_off + inst + 1) - __ldg(p.int_off + inst));
-    float gR;
-    if (p.loss == LRNR_LOSS_MSE) { lp = p.w[0] * R * R / n; gR = 2.0f * p.w[0] * R / n; }
-    else { lp = p.w[0] * fabsf(R); gR = p.w[0] * (float)((R > 0.0f) - (R < 0.0f)); }
-    if (!act) { lp = 0.0f; gR = 0.0f; }
-    ub[0] = -rho * (1.0f - 2.0f * u[0]) * gR;
-    ub[1] = gR;
-    ub[2] = beta * gR;
-    ub[3] = -nu * gR;
-  } else if (T.kind == KIND_IC) {
-    const float B = u[0] - sinf(x);
-    if (!p.grad) {
-      if (act && p.res_ic) p.res_ic[T.first + tid] = B;
-      return;
-    }
-    const float n = (float)(__ldg(p.ic_off + inst + 1) - __ldg(p.ic_off + inst));
-    float gB;
-    if (p.loss == LRNR_LOSS_MSE) { lp = p.w[1] * B * B / n; gB = 2.0f * p.w[1] * B / n; }
-    else { lp = p.w[1] * fabsf(B); gB = p.w[1] * (float)((B > 0.0f) - (B < 0.0f)); }
-    if (!act) { lp = 0.0f; gB = 0.0f; }
-    ub[0] = gB;
-  } else {
-    const float uo = __shfl_xor_sync(0xffffffffu, u[0], 1);
-    const float B = side ? (uo - u[0]) : (u[0] - uo);
-    if (!p.grad) {
-      if (act && side == 0 && p.res_bc) p.res_bc[T.first + (tid >> 1)] = B;
-      return;
-    }
-    const float n = (float)(__ldg(p.bc_off + inst + 1) - __ldg(p.bc_off + inst));
-    float gB;
-    if (p.loss == LRNR_LOSS_MSE) { lp = p.w[2] * B * B / n; gB = 2.0f * p.w[2] * B / n; }
-    else { lp = p.w[2] * fabsf(B); gB = p.w[2] * (float)((B > 0.0f) - (B < 0.0f)); }
-    if (!act) { lp = 0.0f; gB = 0.0f; }
-    if (side) lp = 0.0f;
-    ub[0] = side ? -gB : gB;
-  }
+  float ub[4], lp;
+  if (!residual_and_seeds(p, T, pt, tid, u, ub, lp)) return;
 
   const int DB0 = partial_db0(L, RM);
   {

@@ -56,3 +56,18 @@ def install_fast(P, model, rows, Xis):
 
 def per_instance_rel(a, b):
     return max(rel(a[i], b[i]) for i in range(b.shape[0]))
+
+
+def bc_err(got, Bbc, model, bt, form):
+    """Error of the periodic residual B = u(0,t) - u(2pi,t).  B is a difference of
+    nearly equal values, so its FP32 error is set by the error of its operands:
+    measure ||dB|| against ||u(0, t)|| (the operand scale), not against ||B||."""
+    fwd = lrnr64.full_forward if form == "full" else lrnr64.fast_forward
+    scale = 0.0
+    for i in range(bt.n_inst):
+        inst = bt.instance(i)
+        if len(inst["t_bc"]):
+            u0, _ = fwd(model, inst["s"], np.zeros_like(inst["t_bc"]), inst["t_bc"])
+            scale += float(np.sum(u0[:, 0] ** 2))
+    d = np.linalg.norm(np.asarray(got, np.float64) - Bbc)
+    return d / np.sqrt(scale) if scale > 0 else d
