@@ -35,8 +35,8 @@ WORKLOAD = ("CDR beta=5 nu=1 rho=2; LRNR L=5 hidden layers, M=256, r=16, tanh; F
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
     return ap.parse_args()
@@ -387,8 +387,12 @@ def main():
     # ---- variants: full-width FP32 LRNR residual + gradient, fast residual + gradient
     variants = {}
     P.lrnr_timing(model, True)
-    for form, prec in (("full", "fp32"), ("fast", "fp32")):
-        out = P.lrnr_residual_grad(model, form, prec, db)
+    for form, prec in (("full", "fp32"), ("full", "bf16"), ("full", "bf16x3"), ("fast", "fp32")):
+        try:
+            out = P.lrnr_residual_grad(model, form, prec, db)
+        except P.LrnrError as e:
+            variants[f"{form}_{prec}"] = {"unavailable": str(e)}
+            continue
         torch.cuda.synchronize()
         P.lrnr_timing_read(model)
         nrep = 5 if form == "full" else 50
@@ -402,6 +406,10 @@ def main():
             "points_per_s": n_pts / (step_ms * 1e-3), "ms_per_call": step_ms, "kernel_ms": kms,
             "tflops": fl / (kms * 1e-3) / 1e12, "frac_fp32_peak": fl / (kms * 1e-3) / 1e12 / peak,
             "hbm_gbs": (n_pts * 8) / (kms * 1e-3) / 1e9}
+        if prec != "fp32":
+            products = 3 if prec == "bf16x3" else 1
+            variants[f"{form}_{prec}"]["frac_bf16_peak"] = (
+                products * fl / (kms * 1e-3) / 1e12 / float(peaks.get("bf16_tflops", 1900.0)))
     P.lrnr_timing(model, False)
 
     # ---- errors against the FP64 oracle (full batch, same inputs)
@@ -423,11 +431,14 @@ def main():
             assert np.array_equal(p, rows_all[l]), "EIM rows differ from the oracle"
             Xis.append(Xi)
         fnet = lrnr64.make_fast(net, rows_all, Xis)
-        for form, ref in (("fast", fnet), ("full", net)):
-            lo, ds, dbb = P.lrnr_residual_grad(model, form, "fp32", db)
+        for form, ref, precs in (("fast", fnet, ("fp32",)), ("full", net, ("fp32", "bf16", "bf16x3"))):
             ro, rs, rb = lrnr64.residual_grad(ref, bt32, form)
-            variants[f"{form}_fp32"]["err_vs_fp64_oracle"] = {
-                "loss": rel(lo.cpu(), ro), "dL_ds": rel(ds.cpu(), rs), "dL_db": rel(dbb.cpu(), rb)}
+            for prec in precs:
+                if "unavailable" in variants.get(f"{form}_{prec}", {}):
+                    continue
+                lo, ds, dbb = P.lrnr_residual_grad(model, form, prec, db)
+                variants[f"{form}_{prec}"]["err_vs_fp64_oracle"] = {
+                    "loss": rel(lo.cpu(), ro), "dL_ds": rel(ds.cpu(), rs), "dL_db": rel(dbb.cpu(), rb)}
         variants["fast_fp32"]["eim_rows_bit_exact"] = True
 
     # ---- end to end: host buffers in, loss and s back, through the public API

@@ -196,8 +196,10 @@ lrnr_status lrnr_timing(lrnr_model *m, int enable);
 
 /* lrnr_timing_read -- wait for the recorded events, return the summed kernel time
  * (host, milliseconds) and the number of timed launches since the last read (or
- * since lrnr_timing), and start a new count.  After a CUDA graph replay, read
- * once per replay: the graph re-records the same events. */
+ * since lrnr_timing), and start a new count.  Pairs recorded while the stream was
+ * being captured into a CUDA graph belong to the graph: every replay re-records
+ * them and every read reports them again, so replay the graph once before each
+ * read.  lrnr_timing releases them. */
 lrnr_status lrnr_timing_read(lrnr_model *m, double *ms_total, int64_t *launches);
 
 /* lrnr_last_device_status -- synchronises the device, returns and clears the

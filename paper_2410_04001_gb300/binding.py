@@ -203,6 +203,12 @@ class DeviceBatch:
             t = getattr(self, k)
             setattr(st, k, t.data_ptr() if t is not None and t.numel() else None)
 
+    def with_s(self, s):
+        """A batch sharing these points but reading coefficients from ``s``."""
+        t = dict(self.tensors)
+        t["s"] = s
+        return DeviceBatch(self.n_inst, **t)
+
     @property
     def n_points(self) -> int:
         return int(self.x_int.numel() + self.x_ic.numel() + 2 * self.t_bc.numel())

@@ -24,6 +24,7 @@ void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
                   const int *r, std::vector<unsigned char> &out);
 int full_tc_nt();
+size_t full_tc_scratch_floats(int L, int RM, int grid);
 }  // namespace lrnr
 
 using namespace lrnr;
@@ -53,10 +54,13 @@ struct lrnr_model {
   int *status_dev = nullptr;
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  // optional CUDA-event timing of the tile kernels (one event pair per launch)
+  // optional CUDA-event timing of the tile kernels (one event pair per launch);
+  // pairs recorded while a stream was being captured belong to the CUDA graph and
+  // are re-recorded by each replay, so they are kept until timing is reset
   bool timing = false;
   std::vector<cudaEvent_t> ev_start, ev_stop;
   size_t ev_used = 0;
+  std::vector<cudaEvent_t> cap_start, cap_stop;
 };
 
 namespace {
@@ -219,7 +223,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
       p.nt = full_fp32_choose_nt(m->L, p.RM, partial_len(m->L, p.RM, m->L * m->M + 1));
       if (!p.nt) return LRNR_ENOTSUP;
     } else if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
-      if (!m->tc_pack || !full_tc_supported(m->L, m->M, m->RM)) return LRNR_ENOTSUP;
+      p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
+      if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM)) return LRNR_ENOTSUP;
       p.pack = nullptr;
       p.nt = full_tc_nt();
     } else {
@@ -232,13 +237,17 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   p.P = grad ? partial_len(m->L, p.RM, ps.nb_entries - 1) : 0;
   const int64_t tiles = max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, p.nt);
   if (tiles > INT32_MAX / 2) return LRNR_EINVAL;
-  const size_t need = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1)) +
-                      (grad ? (size_t)tiles * p.P * sizeof(float) : 0);
-  rc = ensure_ws(m, need, st);
+  const bool tc = form == LRNR_FULL && (prec == LRNR_BF16 || prec == LRNR_BF16X3);
+  const int tc_grid = (int)std::min<int64_t>(tiles, m->num_sms);
+  const size_t off_part = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));
+  const size_t part_bytes = grad ? align256((size_t)tiles * p.P * sizeof(float)) : 0;
+  const size_t scr_bytes = tc ? full_tc_scratch_floats(m->L, p.RM, tc_grid) * sizeof(float) : 0;
+  rc = ensure_ws(m, off_part + part_bytes + scr_bytes, st);
   if (rc != LRNR_OK) return rc;
   p.tile_off = reinterpret_cast<int32_t *>(m->ws);
-  p.partial = reinterpret_cast<float *>(static_cast<char *>(m->ws) +
-                                        align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1)));
+  p.partial = reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part);
+  p.scratch = tc ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes) : nullptr;
+  p.max_wait = 1u << 20;
   p.loss = LRNR_LOSS_MSE;
   p.w[0] = p.w[1] = p.w[2] = 1.0f;
   ps.grid_cap = (int)std::min<int64_t>(tiles, INT32_MAX);
@@ -250,7 +259,17 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
   KParams &p = ps.p;
   CK(launch_tile_offsets(p, const_cast<int32_t *>(p.tile_off), st));
   cudaEvent_t e1 = nullptr, e2 = nullptr;
-  if (m->timing) {
+  const bool cap = m->timing && capturing(st);
+  if (cap) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    m->cap_start.push_back(a);
+    m->cap_stop.push_back(b);
+    e1 = a;
+    e2 = b;
+    CK(cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+  } else if (m->timing) {
     if (m->ev_used == m->ev_start.size()) {
       cudaEvent_t a, b;
       CK(cudaEventCreate(&a));
@@ -261,7 +280,7 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
     e1 = m->ev_start[m->ev_used];
     e2 = m->ev_stop[m->ev_used];
     ++m->ev_used;
-    CK(cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal));
+    CK(cudaEventRecord(e1, st));
   }
   if (form == LRNR_FAST) {
     CK(launch_fast(p, ps.grid_cap, st));
@@ -270,7 +289,7 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
   } else {
     CK(launch_full_tc(p, m->tc_pack, (int)prec, ps.grid_cap, st));
   }
-  if (e2) CK(cudaEventRecordWithFlags(e2, st, cudaEventRecordExternal));
+  if (e2) CK(cap ? cudaEventRecordWithFlags(e2, st, cudaEventRecordExternal) : cudaEventRecord(e2, st));
   return LRNR_OK;
 }
 
@@ -382,9 +401,9 @@ lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U, const
   if ((e = cudaMemcpy(m->offs_dev, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&m->status_dev, sizeof(int))) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(m->status_dev, 0, sizeof(int))) != cudaSuccess) return fail(e);
-  if (full_tc_supported(L, M, RM)) {
+  if (full_tc_supported(L, M, std::max(16, RM))) {
     std::vector<unsigned char> tp;
-    full_tc_pack(L, M, RM, m->U, m->V, m->b, m->r, tp);
+    full_tc_pack(L, M, std::max(16, RM), m->U, m->V, m->b, m->r, tp);
     if ((e = cudaMalloc(&m->tc_pack, tp.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(m->tc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   }
@@ -492,6 +511,17 @@ lrnr_status fastlrnr_select_rows(lrnr_model *m, int layer, const double *snapsho
   m->rows[layer].assign(hrows.begin(), hrows.begin() + used);
   m->rhat[layer] = used;
   m->fast_dirty = true;
+  {
+    // once every hidden layer has reduced bases, build the FastLRNR pack here so
+    // later calls (and graph captures) allocate nothing for it
+    bool all = true;
+    for (int l = 0; l < m->L; ++l) all = all && m->rhat[l] > 0;
+    if (all) {
+      rc = build_fast_pack(m);
+      if (rc != LRNR_OK && rc != LRNR_ENOTSUP) { cleanup(); return rc; }
+      rc = LRNR_OK;
+    }
+  }
   if (rows_out) CKC(cudaMemcpyAsync(rows_out, rows_d, sizeof(int32_t) * used, cudaMemcpyDeviceToDevice, st));
   if (Xi_out) CKC(cudaMemcpyAsync(Xi_out, Xi_d, sizeof(double) * (size_t)M * used, cudaMemcpyDeviceToDevice, st));
   CKC(cudaStreamSynchronize(st));
@@ -592,8 +622,13 @@ lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int
 
 lrnr_status lrnr_timing(lrnr_model *m, int enable) {
   if (!m) return LRNR_EINVAL;
+  DeviceGuard g(m->device);
   m->timing = enable != 0;
   m->ev_used = 0;
+  for (auto e : m->cap_start) cudaEventDestroy(e);
+  for (auto e : m->cap_stop) cudaEventDestroy(e);
+  m->cap_start.clear();
+  m->cap_stop.clear();
   return LRNR_OK;
 }
 
@@ -607,8 +642,14 @@ lrnr_status lrnr_timing_read(lrnr_model *m, double *ms_total, int64_t *launches)
     CK(cudaEventElapsedTime(&ms, m->ev_start[i], m->ev_stop[i]));
     tot += ms;
   }
+  for (size_t i = 0; i < m->cap_start.size(); ++i) {
+    CK(cudaEventSynchronize(m->cap_stop[i]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, m->cap_start[i], m->cap_stop[i]));
+    tot += ms;
+  }
   if (ms_total) *ms_total = tot;
-  if (launches) *launches = (int64_t)m->ev_used;
+  if (launches) *launches = (int64_t)(m->ev_used + m->cap_start.size());
   m->ev_used = 0;
   return LRNR_OK;
 }
@@ -643,6 +684,8 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->ws);
   for (auto e : m->ev_start) cudaEventDestroy(e);
   for (auto e : m->ev_stop) cudaEventDestroy(e);
+  for (auto e : m->cap_start) cudaEventDestroy(e);
+  for (auto e : m->cap_stop) cudaEventDestroy(e);
   delete m;
 }
 

@@ -52,6 +52,8 @@ struct KParams {
   float *u, *ut, *ux, *uxx, *res, *res_ic, *res_bc;
   int64_t *step;               // spinprop: incremented once by block 0
   int *status;
+  float *scratch;              // tensor-core path: per-CTA store of layer inputs
+  uint32_t max_wait;           // iteration cap of every device-side wait
 };
 
 // --- layout of the FP32 packs -------------------------------------------------

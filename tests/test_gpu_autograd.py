@@ -1,0 +1,63 @@
+"""torch.autograd wrapper of the adjoint kernel, and the captured SPInProp graph."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import lrnr64
+from tests.gpu_common import TOL_FP32, as_f32_batch, eim_for, install_fast, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_04001_gb300 as P
+    return P
+
+
+@pytest.mark.parametrize("form", ["fast", "full"])
+def test_autograd_gradient_matches_oracle(P, form):
+    from paper_2410_04001_gb300.autograd import lrnr_loss
+    g = synth.rng(4)
+    net = synth.make_net(g, L=3, M=48, r=8)
+    bt = as_f32_batch(synth.make_instances(g, net, 3, 200, 500))
+    rows, Xis, _ = eim_for(net, bt.s[0], 16)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    install_fast(P, model, rows, Xis)
+    db = P.DeviceBatch.from_host(bt)
+    s = db.s.clone().requires_grad_(True)
+    lo = lrnr_loss(s, model, db, form=form)
+    w = torch.tensor([1.0, -2.0, 0.5], device="cuda")
+    (lo * w).sum().backward()
+    ref = lrnr64.make_fast(net, rows, Xis) if form == "fast" else net
+    ro, rs, _ = lrnr64.residual_grad(ref, bt, form)
+    assert rel(lo.detach().cpu(), ro) < TOL_FP32
+    assert rel(s.grad.cpu(), rs * np.array([1.0, -2.0, 0.5])[:, None]) < TOL_FP32
+
+
+def test_captured_spinprop_graph_equals_eager_steps(P):
+    from paper_2410_04001_gb300.graph import SpinpropGraph
+    g = synth.rng(6)
+    net = synth.make_net(g, L=3, M=32, r=8)
+    bt = as_f32_batch(synth.make_instances(g, net, 4, 100, 300))
+    rows, Xis, _ = eim_for(net, bt.s[0], 16)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    install_fast(P, model, rows, Xis)
+    db = P.DeviceBatch.from_host(bt)
+
+    def state():
+        s = db.s.clone()
+        return s, torch.zeros_like(s), torch.zeros_like(s), torch.zeros(1, dtype=torch.int64, device="cuda")
+    s1, m1, v1, k1 = state()
+    for _ in range(6):
+        P.spinprop_step(model, "fast", "fp32", db, s1, m1, v1, k1, 2, lr=1e-2)
+    s2, m2, v2, k2 = state()
+    gr = SpinpropGraph(model, db, s2, m2, v2, k2, n_steps=2, lr=1e-2)   # runs 2 steps eagerly
+    for _ in range(5):
+        gr.replay()
+    torch.cuda.synchronize()
+    assert k1.item() == 12 and k2.item() == 12
+    assert torch.equal(s1, s2) and torch.equal(m1, m2) and torch.equal(v1, v2)
