@@ -57,7 +57,8 @@ typedef enum {
   LRNR_ETIMEOUT = 6,    /* a device wait reached its iteration cap */
   LRNR_ENOTREADY = 7,   /* FastLRNR layers not selected, or workspace too small while capturing */
   LRNR_ENONFINITE = 8,  /* a kernel met a NaN or infinity in its input */
-  LRNR_ENOTSUP = 9      /* the (form, precision) pair is not implemented */
+  LRNR_ENOTSUP = 9,     /* the (form, precision) pair is not implemented */
+  LRNR_ETOOBIG = 10     /* batch larger than the fixed scratch of lrnr_residual_grad_noalloc */
 } lrnr_status;
 
 typedef enum {
@@ -178,6 +179,36 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec,
                           int n_steps, float lr, float beta1, float beta2, float eps,
                           float lambda_loc, const float *s_anchor, float *loss_out,
                           void *stream);
+
+/*
+ * lrnr_residual_grad_noalloc -- the FastLRNR FP32 loss and gradient of
+ * lrnr_residual_grad (form LRNR_FAST, precision LRNR_FP32, same arguments and
+ * results), for callers that cannot allocate device memory: code that runs
+ * while a stream is being captured into a CUDA graph in global mode (cudaMalloc
+ * is refused there), applications whose device memory belongs to another
+ * allocator or a fixed budget, and latency-critical loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc / cudaFree.  It allocates nothing:
+ * its scratch (tile offsets and per-tile partial sums) is a fixed 8 MiB array in
+ * the library's device image, held by every GPU that loads the library until the
+ * process exits.  The paper has no counterpart; this is an interface option.
+ *   Capacity: 4*(n_inst+1) bytes (rounded up to 256) plus one partial row of
+ *     4*(1 + (L+1)*RM + L*RH + 1) bytes per tile of 128 points must fit in 8 MiB
+ *     (RM, RH: rank and EIM rows rounded up to 8 or 16); larger batches return
+ *     LRNR_ETOOBIG before any GPU work.  At L = 5, r = 16, rhat = 16 that is about
+ *     11,500 tiles, i.e. roughly 1.4 million collocation points.
+ *   Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   Sharing: every call uses the same array and leaves its contents behind (all
+ *     of it is rewritten before it is read, nothing relies on zeros); calls whose
+ *     kernels overlap on the GPU (different streams, or several host threads)
+ *     race on it and must be serialised by the caller.
+ *   Requires every hidden layer selected (fastlrnr_select_rows), else
+ *     LRNR_ENOTREADY; the model's own workspace is not used or grown.
+ */
+lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batch *bt, lrnr_loss loss,
+                                       const float *w, float *loss_out, float *dL_ds,
+                                       float *dL_db, void *stream);
 
 /* lrnr_reserve -- size the workspace for batches of up to max_points collocation
  * points (interior + initial + 2 x pairs) in up to max_inst instances.  Call it

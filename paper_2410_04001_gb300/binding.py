@@ -16,7 +16,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblrnr.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, EEARLYSTOP, ETIMEOUT, ENOTREADY, ENONFINITE, ENOTSUP = range(10)
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, EEARLYSTOP, ETIMEOUT, ENOTREADY, ENONFINITE, ENOTSUP, ETOOBIG = range(11)
 FP32, TF32, BF16, BF16X3 = 0, 1, 2, 3
 FULL, FAST = 0, 1
 LOSS_MSE, LOSS_L1 = 0, 1
@@ -58,6 +58,7 @@ _SIGS = {
     "spinprop_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P,
                                      _P, _P, _P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
+    "lrnr_residual_grad_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "lrnr_reserve": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "lrnr_model_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "lrnr_timing": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -291,6 +292,25 @@ def lrnr_residual_grad(model: Model, form: str, prec: str, batch: DeviceBatch, l
                                   _LOSS[loss], ctypes.cast(wa, _P) if wa is not None else None,
                                   _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream))
     _check(rc, "lrnr_residual_grad")
+    return out
+
+
+def lrnr_residual_grad_noalloc(model: Model, batch: DeviceBatch, loss: str = "mse", w=None,
+                               want_db: bool = True, stream=None, out=None):
+    """FastLRNR FP32 loss and gradient computed without any device allocation: the
+    library's fixed 8 MiB scratch replaces the model workspace (for callers that
+    cannot allocate, e.g. inside a global-mode graph capture).  Output buffers are
+    still the caller's; pass ``out`` to reuse them."""
+    dev = batch.x_int.device
+    if out is None:
+        out = (torch.empty(batch.n_inst, dtype=torch.float32, device=dev),
+               torch.empty((batch.n_inst, model.sum_r), dtype=torch.float32, device=dev),
+               torch.empty((batch.n_inst, model.sum_m), dtype=torch.float32, device=dev) if want_db else None)
+    wa = None if w is None else (ctypes.c_float * 3)(*[float(v) for v in w])
+    rc = lib().lrnr_residual_grad_noalloc(model.handle, ctypes.byref(batch.struct), _LOSS[loss],
+                                          ctypes.cast(wa, _P) if wa is not None else None,
+                                          _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream))
+    _check(rc, "lrnr_residual_grad_noalloc")
     return out
 
 

@@ -309,6 +309,7 @@ const char *lrnr_status_string(lrnr_status s) {
     case LRNR_ENOTREADY: return "not ready (FastLRNR layers not selected, or workspace too small while capturing)";
     case LRNR_ENONFINITE: return "non-finite value met by a kernel";
     case LRNR_ENOTSUP: return "form / precision not supported for this model";
+    case LRNR_ETOOBIG: return "batch exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }
@@ -593,6 +594,55 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec, co
   }
   return LRNR_OK;
 }
+
+}  // extern "C"
+
+namespace lrnr {
+// Parameters of a FastLRNR FP32 gradient pass that uses caller-provided scratch
+// instead of the model workspace (for lrnr_residual_grad_noalloc).  Allocates
+// nothing: the reduced pack must already exist.
+lrnr_status noalloc_fast_params(lrnr_model *m, const lrnr_batch *bt, lrnr_loss loss,
+                                const float *w, KParams &p, const int32_t **rows, int *sum_m,
+                                int *device) {
+  lrnr_status rc = check_batch(m, bt);
+  if (rc != LRNR_OK) return rc;
+  if (!bt->s) return LRNR_EINVAL;
+  if (m->fast_dirty || !m->fast_pack) return LRNR_ENOTREADY;
+  std::memset(&p, 0, sizeof(p));
+  p.L = m->L;
+  p.M = m->M;
+  p.n_inst = bt->n_inst;
+  for (int l = 0; l <= m->L; ++l) p.r[l] = m->r[l];
+  for (int l = 0; l <= m->L + 1; ++l) p.roff[l] = m->roff[l];
+  p.sum_r = m->sum_r;
+  p.beta = bt->beta; p.nu = bt->nu; p.rho = bt->rho; p.s = bt->s;
+  p.int_off = bt->int_off; p.ic_off = bt->ic_off; p.bc_off = bt->bc_off;
+  p.x_int = bt->x_int; p.t_int = bt->t_int; p.x_ic = bt->x_ic; p.t_bc = bt->t_bc;
+  p.grad = 1;
+  p.status = m->status_dev;
+  p.RM = m->fRM;
+  p.RH = m->fRH;
+  p.pack = m->fast_pack;
+  p.P = partial_len(m->L, p.RM, m->L * p.RH);
+  // same tile size as lrnr_residual_grad, so both give identical results
+  p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
+  if (!p.nt) return LRNR_ENOTSUP;
+  p.loss = loss;
+  p.w[0] = p.w[1] = p.w[2] = 1.0f;
+  if (w) { p.w[0] = w[0]; p.w[1] = w[1]; p.w[2] = w[2]; }
+  p.max_wait = 1u << 20;
+  *rows = m->rows_dev;
+  *sum_m = m->sum_m;
+  *device = m->device;
+  return LRNR_OK;
+}
+
+int64_t noalloc_max_tiles(const lrnr_batch *bt, int nt) {
+  return max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, nt);
+}
+}  // namespace lrnr
+
+extern "C" {
 
 lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   if (!m || max_points < 0 || max_inst < 1) return LRNR_EINVAL;
