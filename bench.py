@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
+    ap.add_argument("--no-configs", action="store_true", help="skip the batched / SPInProp workloads")
     return ap.parse_args()
 
 
@@ -214,12 +215,22 @@ def run_reference(args):
         Xis.append(Xi)
     fnet = lrnr64.make_fast(net, rows, Xis)
     inst = bt.instance(0)
-    # each step: the oracle SPInProp step on a bounded sample (1/8 of the interior,
-    # initial and periodic points), so that K steps finish in a few minutes
-    sub = dict(inst)
-    sub["x_int"], sub["t_int"] = inst["x_int"][::8], inst["t_int"][::8]
-    sub["x_ic"], sub["t_bc"] = inst["x_ic"][::8], inst["t_bc"][::8]
-    n_pts = len(sub["x_int"]) + len(sub["x_ic"]) + 2 * len(sub["t_bc"])
+
+    def sample(stride):
+        d = dict(inst)
+        d["x_int"], d["t_int"] = inst["x_int"][::stride], inst["t_int"][::stride]
+        d["x_ic"], d["t_bc"] = inst["x_ic"][::stride], inst["t_bc"][::stride]
+        return d, len(d["x_int"]) + len(d["x_ic"]) + 2 * len(d["t_bc"])
+
+    # each step: the oracle SPInProp step on a bounded sample (every stride-th point
+    # of each class), the stride chosen so that warm-up + K steps take about 90 s
+    cal, ncal = sample(8)
+    t0 = time.perf_counter()
+    lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet, cal)
+    per_point = (time.perf_counter() - t0) / ncal
+    budget = 90.0 / max(1, args.steps + args.warmup)
+    stride = max(1, int(np.ceil(bt.n_points * per_point / budget)))
+    sub, n_pts = sample(stride)
     s = inst["s"].copy()
     m = np.zeros_like(s)
     v = np.zeros_like(s)
@@ -243,12 +254,107 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD + "; FastLRNR SPInProp step on a 1/8 point sample", "form": "fast"},
+        "config": {"workload": WORKLOAD + f"; FastLRNR SPInProp step on a 1/{stride} point sample",
+                   "form": "fast"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
-                         "sample": f"every 8th point of each class ({n_pts} points per step)"},
+                         "sample": f"every {stride}th point of each class ({n_pts} points per step)"},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
+
+
+# --------------------------------------------------------------------------- other workloads
+
+def select_rows_on_device(P, model, net, s0, dev, torch, synth):
+    """Device snapshots at the 4 x 3 design plus perturbations, device EIM; returns the
+    snapshot matrices (host, M x K) so the oracle can reduce from the same data."""
+    g = synth.rng(77)
+    xs, ts = synth.snapshot_design(g, 8)
+    xs_d, ts_d = torch.tensor(xs, device=dev), torch.tensor(ts, device=dev)
+    mats = []
+    for l in range(net.L):
+        S = P.lrnr_snapshots(model, l, xs_d, ts_d, torch.tensor(s0[None, :], device=dev))
+        P.fastlrnr_select_rows(model, l, S, 16)
+        mats.append(S.cpu().numpy().T)
+    return mats
+
+
+def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
+    """Batched CDR instances (512, log-uniform counts) and the 1,024-instance SPInProp
+    loop, FastLRNR FP32; plus the fast-phase loop against the same loop on the
+    full-width FP32 LRNR (200 Adam steps on 16 instances)."""
+    out = {}
+    # 512 instances, ~7.9 M points, one residual + gradient pass
+    net, bt = synth.workload_batched()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    mats = select_rows_on_device(P, model, net, bt.s[0], dev, torch, synth)
+    db = P.DeviceBatch.from_host(bt, dev)
+    res = P.lrnr_residual_grad(model, "fast", "fp32", db)
+    P.lrnr_timing(model, True)
+    ts_, km, kn = timed_steps(lambda: P.lrnr_residual_grad(model, "fast", "fp32", db, out=res), 10, model)
+    P.lrnr_timing(model, False)
+    ms = sum(ts_) / len(ts_)
+    r = {"workload": "512 CDR instances, counts log-uniform [1,024, 65,536], M=256 r=16 L=5 rhat=16",
+         "points": db.n_points, "points_per_s": db.n_points / (ms * 1e-3), "ms_per_call": ms,
+         "kernel_ms": km / max(1, kn)}
+    if with_oracle:
+        from oracle import eim64, lrnr64
+        rows, Xis = [], []
+        for S in mats:
+            p_, Xi, _ = eim64.eim_greedy(S, 16)
+            rows.append(p_)
+            Xis.append(Xi)
+        fnet = lrnr64.make_fast(net, rows, Xis)
+        f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        errs = []
+        for i in (0, 255, 511):
+            inst = bt.instance(i)
+            inst = {k: (f32(v) if isinstance(v, np.ndarray) else float(np.float32(v))) for k, v in inst.items()}
+            ro, rs, _ = lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet, inst)
+            ds = res[1][i].cpu().numpy()
+            errs.append(float(np.linalg.norm(ds - rs) / np.linalg.norm(rs)))
+        r["err_dL_ds_sampled_instances"] = max(errs)
+    out["batched_512_fast_fp32"] = r
+    del model, db, res
+    # 1,024 instances x 16,384 points, fused SPInProp steps
+    net, bt = synth.workload_spinprop()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    select_rows_on_device(P, model, net, bt.s[0], dev, torch, synth)
+    db = P.DeviceBatch.from_host(bt, dev)
+    s = db.s.clone()
+    m, v = torch.zeros_like(s), torch.zeros_like(s)
+    k = torch.zeros(1, dtype=torch.int64, device=dev)
+    P.spinprop_step(model, "fast", "fp32", db, s, m, v, k, 2)
+    ts_, _, _ = timed_steps(lambda: P.spinprop_step(model, "fast", "fp32", db, s, m, v, k, 1), 10)
+    ms = sum(ts_) / len(ts_)
+    out["spinprop_1024_fast_fp32"] = {
+        "workload": "1,024 CDR instances x 16,384 points, M=512 r=16 L=5 rhat=16, one Adam step",
+        "points": db.n_points, "steps_per_s": 1e3 / ms, "points_per_s": db.n_points / (ms * 1e-3),
+        "ms_per_step": ms}
+    # fast phase vs full-width fine-tune: 200 Adam steps on the first 16 instances
+    from paper_2410_04001_gb300 import shard
+    sub = shard.subset(bt, 0, 16)
+    dsub = P.DeviceBatch.from_host(sub, dev)
+    cmp = {}
+    for form in ("fast", "full"):
+        s = dsub.s.clone()
+        m, v = torch.zeros_like(s), torch.zeros_like(s)
+        k = torch.zeros(1, dtype=torch.int64, device=dev)
+        lo = torch.zeros(16, dtype=torch.float32, device=dev)
+        P.spinprop_step(model, form, "fp32", dsub, s, m, v, k, 1, loss_out=lo)
+        torch.cuda.synchronize()
+        l0 = float(lo.mean())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.spinprop_step(model, form, "fp32", dsub, s, m, v, k, 199, loss_out=lo)
+        e1.record()
+        torch.cuda.synchronize()
+        # residual loss of the final s, always measured on the full-width LRNR
+        lf, _, _ = P.lrnr_residual_grad(model, "full", "fp32", dsub.with_s(s), want_db=False)
+        cmp[form] = {"steps_per_s": 199e3 / e0.elapsed_time(e1), "loss_first_step": l0,
+                     "final_full_lrnr_loss": float(lf.mean())}
+    out["spinprop_fast_vs_full_16_instances"] = cmp
+    return out
 
 # --------------------------------------------------------------------------- our arm
 
@@ -440,6 +546,11 @@ def main():
                 variants[f"{form}_{prec}"]["err_vs_fp64_oracle"] = {
                     "loss": rel(lo.cpu(), ro), "dL_ds": rel(ds.cpu(), rs), "dL_db": rel(dbb.cpu(), rb)}
         variants["fast_fp32"]["eim_rows_bit_exact"] = True
+
+    # ---- the larger workloads (one GPU): batched instances and the SPInProp loop
+    if not args.no_configs:
+        variants.update(config_variants(P, synth, np, torch, dev, timed_steps, peak,
+                                        with_oracle=(rank == 0 and not args.no_oracle)))
 
     # ---- end to end: host buffers in, loss and s back, through the public API
     host = {k: t.detach().cpu().pin_memory() for k, t in db.tensors.items()}

@@ -188,14 +188,17 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec,
  * is refused there), applications whose device memory belongs to another
  * allocator or a fixed budget, and latency-critical loops that cannot afford the
  * device-wide synchronisation of cudaMalloc / cudaFree.  It allocates nothing:
- * its scratch (tile offsets and per-tile partial sums) is a fixed 8 MiB array in
- * the library's device image, held by every GPU that loads the library until the
- * process exits.  The paper has no counterpart; this is an interface option.
+ * its scratch (tile offsets, per-tile partial sums and the kernel's per-CTA
+ * layer-input store) is a fixed 32 MiB array in the library's device image, held
+ * by every GPU that loads the library until the process exits.  The paper has no
+ * counterpart; this is an interface option.
  *   Capacity: 4*(n_inst+1) bytes (rounded up to 256) plus one partial row of
- *     4*(1 + (L+1)*RM + L*RH + 1) bytes per tile of 128 points must fit in 8 MiB
- *     (RM, RH: rank and EIM rows rounded up to 8 or 16); larger batches return
- *     LRNR_ETOOBIG before any GPU work.  At L = 5, r = 16, rhat = 16 that is about
- *     11,500 tiles, i.e. roughly 1.4 million collocation points.
+ *     4*(1 + (L+1)*RM + L*RH + 1) bytes per tile of 128 points, plus the store of
+ *     at least one CTA (4*4*(L-1)*RM*128 bytes), must fit in 32 MiB (RM, RH: rank
+ *     and EIM rows rounded up to 8 or 16); larger batches return LRNR_ETOOBIG
+ *     before any GPU work.  The grid shrinks to the CTAs whose stores fit, so
+ *     large batches run on fewer SMs; results do not depend on the grid.  At
+ *     L = 5, r = rhat = 16 the batch limit is about 5.8 million points.
  *   Set-up: the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

@@ -211,7 +211,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     p.RM = m->fRM;
     p.RH = m->fRH;
     p.pack = m->fast_pack;
-    // 128 points per tile unless the per-point layer store would not fit
+    for (int l = 0; l < m->L; ++l) p.rh[l] = m->rhat[l];
     p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
     if (!p.nt) return LRNR_ENOTSUP;
     ps.nb_entries = m->L * p.RH + 1;
@@ -238,19 +238,26 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   const int64_t tiles = max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, p.nt);
   if (tiles > INT32_MAX / 2) return LRNR_EINVAL;
   const bool tc = form == LRNR_FULL && (prec == LRNR_BF16 || prec == LRNR_BF16X3);
-  const int tc_grid = (int)std::min<int64_t>(tiles, m->num_sms);
+  ps.grid_cap = (int)std::min<int64_t>(tiles, INT32_MAX);
+  size_t scr_bytes = 0;
+  if (tc) {
+    ps.grid_cap = (int)std::min<int64_t>(tiles, m->num_sms);
+    scr_bytes = full_tc_scratch_floats(m->L, p.RM, ps.grid_cap) * sizeof(float);
+  } else if (form == LRNR_FAST) {
+    // the FastLRNR kernel keeps layer inputs in a per-CTA scratch: size the grid first
+    ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)fast_ctas_per_sm(p) * m->num_sms);
+    if (grad) scr_bytes = fast_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap) * sizeof(float);
+  }
   const size_t off_part = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));
   const size_t part_bytes = grad ? align256((size_t)tiles * p.P * sizeof(float)) : 0;
-  const size_t scr_bytes = tc ? full_tc_scratch_floats(m->L, p.RM, tc_grid) * sizeof(float) : 0;
   rc = ensure_ws(m, off_part + part_bytes + scr_bytes, st);
   if (rc != LRNR_OK) return rc;
   p.tile_off = reinterpret_cast<int32_t *>(m->ws);
   p.partial = reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part);
-  p.scratch = tc ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes) : nullptr;
+  p.scratch = scr_bytes ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes) : nullptr;
   p.max_wait = 1u << 20;
   p.loss = LRNR_LOSS_MSE;
   p.w[0] = p.w[1] = p.w[2] = 1.0f;
-  ps.grid_cap = (int)std::min<int64_t>(tiles, INT32_MAX);
   return LRNR_OK;
 }
 
@@ -623,6 +630,7 @@ lrnr_status noalloc_fast_params(lrnr_model *m, const lrnr_batch *bt, lrnr_loss l
   p.RM = m->fRM;
   p.RH = m->fRH;
   p.pack = m->fast_pack;
+  for (int l = 0; l < m->L; ++l) p.rh[l] = m->rhat[l];
   p.P = partial_len(m->L, p.RM, m->L * p.RH);
   // same tile size as lrnr_residual_grad, so both give identical results
   p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
@@ -651,7 +659,11 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   const int64_t tiles = max_points / nt_min + 3 * (int64_t)max_inst + 3;
   int Pmax = partial_len(m->L, m->RM, m->L * m->M + 1);
   Pmax = std::max(Pmax, partial_len(m->L, RMAX, m->L * RHMAX + 1));
-  const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) + (size_t)tiles * Pmax * sizeof(float);
+  // per-CTA layer-input stores (tensor-core and FastLRNR kernels): at most 4 CTAs per SM
+  const size_t store = std::max(full_tc_scratch_floats(m->L, RMAX, m->num_sms),
+                                fast_scratch_floats(m->L, RMAX, 128, 4 * m->num_sms));
+  const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) +
+                      align256((size_t)tiles * Pmax * sizeof(float)) + store * sizeof(float);
   return ensure_ws(m, need, nullptr);
 }
 

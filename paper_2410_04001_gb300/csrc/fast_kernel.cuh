@@ -2,13 +2,16 @@
 //
 // One thread per collocation point.  The reduced bases (Uhat, bhat, Vhat: a few KB
 // per layer) and the tile's coefficients s live in shared memory and are read
-// with warp-uniform (broadcast) loads; every per-point quantity -- the jet of the
-// reduced state zhat (value, d/dt, d/dx, d2/dx2) and its adjoint -- stays in
-// registers.  The forward stores each hidden layer's input jet in shared memory
-// ([slot][thread], conflict free) so the reverse sweep can rebuild the layer's
-// pre-activation without re-running the network.  Per-layer gradient pieces are
-// summed over the warp by recursive halving and over the tile's warps in a fixed
-// order, giving one partial row per tile.
+// with warp-uniform (broadcast) loads.  Each layer streams over its rhat rows: for
+// row i the thread forms the pre-activation jet a_i = Uhat_i . (s * zhat) (+ bhat_i)
+// (four scalars, one per jet channel), pushes it through tanh and accumulates the
+// next rank-r jet zhat' += Vhat_i w_i; the reverse sweep does the same per row for
+// the adjoint.  Row loops are not unrolled, which keeps the kernel small enough for
+// the instruction cache.  The forward keeps each hidden layer's input jet in a
+// per-CTA global scratch area ([slot][thread], coalesced, L2-resident) so the
+// reverse sweep can rebuild pre-activations without re-running the network.
+// Per-layer gradient pieces are summed over the warp and over the tile's warps in
+// a fixed order, giving one partial row per tile.
 #pragma once
 
 #include <algorithm>
@@ -19,31 +22,35 @@
 
 namespace lrnr {
 
-// Shared memory of one CTA (floats): the reduced bases, the tile's s, the stored
-// layer inputs [(l-1)*4 + c][k][thread], the adjoint staging [c][i][thread] and
-// one partial row per warp.
+// Shared memory of one CTA (floats): the reduced bases, the tile's s, the staged
+// pre-activation adjoints of the current layer [row][thread][channel] and one
+// partial row per warp.
 struct FastLayout {
-  int pack, s, q, ab, red, total;
+  int pack, s, ab, red, total;
   __host__ __device__ FastLayout(int L, int RM, int RH, int NT, int P) {
     pack = 0;
     s = (fast_pack_floats(L, RM, RH) + 3) & ~3;
-    q = s + (L + 1) * RM;
-    ab = q + (L > 1 ? (L - 1) : 0) * 4 * RM * NT;
+    ab = (s + (L + 1) * RM + 3) & ~3;
     red = ab + 4 * RH * NT;
     total = red + (NT / 32) * P;
   }
 };
 
+// Floats of layer-input store per CTA (global scratch).
+__host__ __device__ inline size_t fast_store_floats(int L, int RM, int NT) {
+  return (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * NT;
+}
+
 // The input jet of hidden layer l: stored by the forward (l > 0) or rebuilt from
 // the point (l == 0: zhat^0 = V^0^T z^0).
 template <int RM, int C>
-__device__ __forceinline__ void load_input(int l, const float *__restrict__ q_s, int NT, int tid,
+__device__ __forceinline__ void load_input(int l, const float *__restrict__ q_g, int NT, int tid,
                                            const float *V0, float x, float t, float (&q)[C][RM]) {
   if (l > 0) {
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int k = 0; k < RM; ++k) q[c][k] = q_s[(((l - 1) * 4 + c) * RM + k) * NT + tid];
+      for (int k = 0; k < RM; ++k) q[c][k] = q_g[(((l - 1) * 4 + c) * RM + k) * NT + tid];
   } else {
 #pragma unroll
     for (int c = 0; c < C; ++c)
@@ -63,30 +70,30 @@ __device__ __forceinline__ void load_input(int l, const float *__restrict__ q_s,
 // out[c] += W[0..NI) . v[c][0..NI)
 template <int RM, int NI, int C>
 __device__ __forceinline__ void row_dot(const float *__restrict__ W, const float (&v)[C][RM],
-                                        float (&out)[C][1]) {
+                                        float (&out)[C]) {
   if constexpr (NI % 4 == 0) {
 #pragma unroll
     for (int k = 0; k < NI; k += 4) {
       const float4 w = *reinterpret_cast<const float4 *>(W + k);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        out[c][0] = fmaf(w.x, v[c][k], out[c][0]);
-        out[c][0] = fmaf(w.y, v[c][k + 1], out[c][0]);
-        out[c][0] = fmaf(w.z, v[c][k + 2], out[c][0]);
-        out[c][0] = fmaf(w.w, v[c][k + 3], out[c][0]);
+        out[c] = fmaf(w.x, v[c][k], out[c]);
+        out[c] = fmaf(w.y, v[c][k + 1], out[c]);
+        out[c] = fmaf(w.z, v[c][k + 2], out[c]);
+        out[c] = fmaf(w.w, v[c][k + 3], out[c]);
       }
     }
   } else {
 #pragma unroll
     for (int k = 0; k < NI; ++k)
 #pragma unroll
-      for (int c = 0; c < C; ++c) out[c][0] = fmaf(W[k], v[c][k], out[c][0]);
+      for (int c = 0; c < C; ++c) out[c] = fmaf(W[k], v[c][k], out[c]);
   }
 }
 
 // acc[c][0..NI) += W[0..NI) * v[c]
 template <int RM, int NI, int C>
-__device__ __forceinline__ void row_axpy(const float *__restrict__ W, const float (&v)[C][1],
+__device__ __forceinline__ void row_axpy(const float *__restrict__ W, const float (&v)[C],
                                          float (&acc)[C][RM]) {
   if constexpr (NI % 4 == 0) {
 #pragma unroll
@@ -94,24 +101,114 @@ __device__ __forceinline__ void row_axpy(const float *__restrict__ W, const floa
       const float4 w = *reinterpret_cast<const float4 *>(W + k);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        acc[c][k] = fmaf(w.x, v[c][0], acc[c][k]);
-        acc[c][k + 1] = fmaf(w.y, v[c][0], acc[c][k + 1]);
-        acc[c][k + 2] = fmaf(w.z, v[c][0], acc[c][k + 2]);
-        acc[c][k + 3] = fmaf(w.w, v[c][0], acc[c][k + 3]);
+        acc[c][k] = fmaf(w.x, v[c], acc[c][k]);
+        acc[c][k + 1] = fmaf(w.y, v[c], acc[c][k + 1]);
+        acc[c][k + 2] = fmaf(w.z, v[c], acc[c][k + 2]);
+        acc[c][k + 3] = fmaf(w.w, v[c], acc[c][k + 3]);
       }
     }
   } else {
 #pragma unroll
     for (int k = 0; k < NI; ++k)
 #pragma unroll
-      for (int c = 0; c < C; ++c) acc[c][k] = fmaf(W[k], v[c][0], acc[c][k]);
+      for (int c = 0; c < C; ++c) acc[c][k] = fmaf(W[k], v[c], acc[c][k]);
+  }
+}
+
+// tanh jet of one row, in place: a = (a0, a_t, a_x, a_xx) -> (z, z_t, z_x, z_xx).
+template <int C>
+__device__ __forceinline__ void jet_fwd(float (&a)[C]) {
+  float z, d1, d2;
+  tanh_d(a[0], z, d1, d2);
+  if constexpr (C == 4) a[3] = d2 * a[2] * a[2] + d1 * a[3];
+  if constexpr (C >= 3) {
+    a[1] *= d1;
+    a[2] *= d1;
+  }
+  a[0] = z;
+}
+
+// Adjoint of jet_fwd: given the pre-activation a and the output adjoint wb,
+// overwrite wb with the pre-activation adjoint.
+template <int C>
+__device__ __forceinline__ void jet_bwd(const float (&a)[C], float (&wb)[C]) {
+  float z, d1, d2;
+  tanh_d(a[0], z, d1, d2);
+  float ab0 = wb[0] * d1;
+  if constexpr (C >= 3) ab0 += d2 * (wb[1] * a[1] + wb[2] * a[2]);
+  if constexpr (C == 4) {
+    const float d3 = d1 * (6.0f * z * z - 2.0f);
+    ab0 += wb[3] * (d3 * a[2] * a[2] + d2 * a[3]);
+    wb[2] = wb[2] * d1 + 2.0f * wb[3] * d2 * a[2];
+    wb[3] = wb[3] * d1;
+  } else if constexpr (C >= 3) {
+    wb[2] = wb[2] * d1;
+  }
+  if constexpr (C >= 3) wb[1] = wb[1] * d1;
+  wb[0] = ab0;
+}
+
+// One reduced layer forward: y (= s * zhat, input jet) -> qn (next rank-r jet).
+template <int RM, int C, int NI, int NO>
+__device__ __forceinline__ void layer_fwd(const float *__restrict__ Uh, const float *__restrict__ bh,
+                                          const float *__restrict__ Vh, int nrows,
+                                          const float (&y)[C][RM], float (&qn)[C][RM]) {
+#pragma unroll 1
+  for (int i = 0; i < nrows; ++i) {
+    float a[C];
+    a[0] = bh[i];
+#pragma unroll
+    for (int c = 1; c < C; ++c) a[c] = 0.0f;
+    row_dot<RM, NI, C>(Uh + i * RM, y, a);
+    jet_fwd<C>(a);
+    row_axpy<RM, NO, C>(Vh + i * RM, a, qn);
+  }
+}
+
+// One reduced layer reverse, in two passes over the rows so that no more than two
+// rank-r jets are live at once:
+//   pass 1: rebuild a_i = Uhat_i . y (+ bhat_i), pull wb_i = Vhat_i . qb back through
+//           the tanh jet, stage abar_i (all channels) in ab_s[row][thread][channel];
+//   pass 2: pb = Uhat^T abar from the staged rows.
+template <int RM, int C, int NI, int NO>
+__device__ __forceinline__ void layer_bwd(const float *__restrict__ Uh, const float *__restrict__ bh,
+                                          const float *__restrict__ Vh, int nrows,
+                                          const float (&y)[C][RM], const float (&qb)[C][RM],
+                                          float4 *ab_s, int NT) {
+#pragma unroll 1
+  for (int i = 0; i < nrows; ++i) {
+    float a[C], wb[C];
+    a[0] = bh[i];
+#pragma unroll
+    for (int c = 1; c < C; ++c) a[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) wb[c] = 0.0f;
+    row_dot<RM, NI, C>(Uh + i * RM, y, a);
+    row_dot<RM, NO, C>(Vh + i * RM, qb, wb);
+    jet_bwd<C>(a, wb);
+    float4 v = make_float4(wb[0], 0.0f, 0.0f, 0.0f);
+    if constexpr (C == 4) v = make_float4(wb[0], wb[1], wb[2], wb[3]);
+    ab_s[i * NT + threadIdx.x] = v;
+  }
+}
+
+template <int RM, int C, int NI>
+__device__ __forceinline__ void layer_bwd_pbar(const float *__restrict__ Uh, int nrows,
+                                               const float4 *ab_s, int NT, float (&pb)[C][RM]) {
+#pragma unroll 2
+  for (int i = 0; i < nrows; ++i) {
+    const float4 v = ab_s[i * NT + threadIdx.x];
+    float ab[C];
+    ab[0] = v.x;
+    if constexpr (C == 4) { ab[1] = v.y; ab[2] = v.z; ab[3] = v.w; }
+    row_axpy<RM, NI, C>(Uh + i * RM, ab, pb);
   }
 }
 
 template <int RM, int RH, int C>
 __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restrict__ w_s,
-                          const float *__restrict__ s_s, float *__restrict__ q_s,
-                          float *__restrict__ ab_s, float *red_w) {
+                          const float *__restrict__ s_s, float *__restrict__ q_g, float4 *ab_s,
+                          float *red_w) {
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
   const int L = p.L;
@@ -120,25 +217,12 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
   const float Uout = w_s[L * LS + 2 * R1];
   const float bout = w_s[L * LS + 2 * R1 + 1];
 
-  // ---- the point
   const PointIn pt = load_point(p, T, tid);
   const float x = pt.x, t = pt.t;
 
   // ---- forward: zhat^0 = V^0^T z^0, then the reduced layers (Eq. 2.8)
   float q[C][RM];
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-#pragma unroll
-    for (int k = 0; k < RM; ++k) q[c][k] = 0.0f;
-#pragma unroll
-  for (int k = 0; k < R1; ++k) {
-    q[0][k] = V0[k] * x + V0[R1 + k] * t;
-    if constexpr (C >= 3) {
-      q[1][k] = V0[R1 + k];
-      q[2][k] = V0[k];
-    }
-  }
-
+  load_input<RM, C>(0, q_g, NT, tid, V0, x, t, q);
   for (int l = 0; l < L; ++l) {
     const float *Uh = w_s + l * LS;
     const float *bh = Uh + RH * RM;
@@ -148,31 +232,21 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < RM; ++k) q_s[(((l - 1) * 4 + c) * RM + k) * NT + tid] = q[c][k];
+        for (int k = 0; k < RM; ++k) q_g[(((l - 1) * 4 + c) * RM + k) * NT + tid] = q[c][k];
     }
-    float a[C][RH];
+    float y[C][RM];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int i = 0; i < RH; ++i) a[c][i] = (c == 0) ? bh[i] : 0.0f;
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < RM; ++k) q[c][k] *= sl[k];
-    if (l == 0) mv_rows<RM, R1, RH, C>(Uh, q, a);
-    else mv_rows<RM, RM, RH, C>(Uh, q, a);
-    act_fwd<C, RH>(a);
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < RM; ++k) q[c][k] = 0.0f;
-    if (l == L - 1) mv_cols<RM, RH, 1, C, RH>(Vh, a, q);
-    else mv_cols<RM, RH, RM, C, RH>(Vh, a, q);
+      for (int k = 0; k < RM; ++k) { y[c][k] = q[c][k] * sl[k]; q[c][k] = 0.0f; }
+    const int nr = p.rh[l];
+    if (l == 0 && l == L - 1) layer_fwd<RM, C, R1, 1>(Uh, bh, Vh, nr, y, q);
+    else if (l == 0) layer_fwd<RM, C, R1, RM>(Uh, bh, Vh, nr, y, q);
+    else if (l == L - 1) layer_fwd<RM, C, RM, 1>(Uh, bh, Vh, nr, y, q);
+    else layer_fwd<RM, C, RM, RM>(Uh, bh, Vh, nr, y, q);
   }
   const float sL = s_s[L * RM];
-  float u[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) u[c] = 0.0f;
+  float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0];
   u[0] += bout;
@@ -183,25 +257,22 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
 
   // ---- reverse sweep (backpropagation through the FastLRNR, Sec. 2.3)
   const int DB0 = partial_db0(L, RM);
-  {
-    const float ls = warp_sum(lp);
-    if ((tid & 31) == 0) red_w[0] += ls;
-  }
   float qb[C][RM];
   {
+    const float ls = warp_sum(lp);
     float dsL = 0.0f;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const float pb = Uout * ub[c];
-      dsL += pb * q[c][0];
+      const float pbv = Uout * ub[c];
+      dsL += pbv * q[c][0];
 #pragma unroll
       for (int k = 0; k < RM; ++k) qb[c][k] = 0.0f;
-      qb[c][0] = sL * pb;
+      qb[c][0] = sL * pbv;
     }
-    float v2[2] = {dsL, ub[0]};
-    const float s0 = warp_sum(v2[0]);
-    const float s1 = warp_sum(v2[1]);
+    const float s0 = warp_sum(dsL);
+    const float s1 = warp_sum(ub[0]);
     if ((tid & 31) == 0) {
+      red_w[0] += ls;
       red_w[1 + L * RM] += s0;
       red_w[DB0 + L * RH] += s1;
     }
@@ -211,53 +282,51 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
     const float *bh = Uh + RH * RM;
     const float *Vh = bh + RH;
     const float *sl = s_s + l * RM;
-    // y = s * (the layer's input jet)
-    float y[C][RM];
-    load_input<RM, C>(l, q_s, NT, tid, V0, x, t, y);
+    const int nr = p.rh[l];
+    {
+      float y[C][RM];
+      load_input<RM, C>(l, q_g, NT, tid, V0, x, t, y);
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+      for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int k = 0; k < RM; ++k) y[c][k] *= sl[k];
-    // row by row: rebuild the pre-activation, pull back the output adjoint
-    // wb = Vhat qb through tanh, stage abar in shared memory
-    float g[RM + RH];
-#pragma unroll
-    for (int i = 0; i < RH; ++i) {
-      float a[C][1], wb[C][1];
-#pragma unroll
-      for (int c = 0; c < C; ++c) { a[c][0] = (c == 0) ? bh[i] : 0.0f; wb[c][0] = 0.0f; }
-      if (l == 0) row_dot<RM, R1, C>(Uh + i * RM, y, a);
-      else row_dot<RM, RM, C>(Uh + i * RM, y, a);
-      if (l == L - 1) row_dot<RM, 1, C>(Vh + i * RM, qb, wb);
-      else row_dot<RM, RM, C>(Vh + i * RM, qb, wb);
-      act_bwd<C, 1>(a, wb);
-#pragma unroll
-      for (int c = 0; c < C; ++c) ab_s[(c * RH + i) * NT + tid] = wb[c][0];
-      g[RM + i] = wb[0][0];
+        for (int k = 0; k < RM; ++k) y[c][k] *= sl[k];
+      if (l == 0 && l == L - 1) layer_bwd<RM, C, R1, 1>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
+      else if (l == 0) layer_bwd<RM, C, R1, RM>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
+      else if (l == L - 1) layer_bwd<RM, C, RM, 1>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
+      else layer_bwd<RM, C, RM, RM>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
     }
-    // pbar = Uhat^T abar
     float pb[C][RM];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
       for (int k = 0; k < RM; ++k) pb[c][k] = 0.0f;
+    if (l == 0) layer_bwd_pbar<RM, C, R1>(Uh, nr, ab_s, NT, pb);
+    else layer_bwd_pbar<RM, C, RM>(Uh, nr, ab_s, NT, pb);
+    // dL/ds^l = sum_c pbar_c * zhat_c (input jet, reloaded) and dL/dbhat^l rows
+    float g[RM + RH];
+    if (l > 0) {
+      // read the stored input jet element by element (keeps one rank-r jet live)
 #pragma unroll
-    for (int i = 0; i < RH; ++i) {
-      float ab[C][1];
+      for (int k = 0; k < RM; ++k) {
+        float d = 0.0f;
 #pragma unroll
-      for (int c = 0; c < C; ++c) ab[c][0] = ab_s[(c * RH + i) * NT + tid];
-      if (l == 0) row_axpy<RM, R1, C>(Uh + i * RM, ab, pb);
-      else row_axpy<RM, RM, C>(Uh + i * RM, ab, pb);
+        for (int c = 0; c < C; ++c)
+          d = fmaf(pb[c][k], q_g[(((l - 1) * 4 + c) * RM + k) * NT + tid], d);
+        g[k] = d;
+      }
+    } else {
+      float y[C][RM];
+      load_input<RM, C>(0, q_g, NT, tid, V0, x, t, y);
+#pragma unroll
+      for (int k = 0; k < RM; ++k) {
+        float d = 0.0f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) d = fmaf(pb[c][k], y[c][k], d);
+        g[k] = d;
+      }
     }
-    // dL/ds^l = sum_c pbar_c * q_c
-    load_input<RM, C>(l, q_s, NT, tid, V0, x, t, y);
 #pragma unroll
-    for (int k = 0; k < RM; ++k) {
-      float d = 0.0f;
-#pragma unroll
-      for (int c = 0; c < C; ++c) d = fmaf(pb[c][k], y[c][k], d);
-      g[k] = d;
-    }
+    for (int i = 0; i < RH; ++i) g[RM + i] = (i < nr) ? ab_s[i * NT + tid].x : 0.0f;
     warp_accumulate<RM + RH>(g, red_w, [&](int j) {
       return j < RM ? 1 + l * RM + j : DB0 + l * RH + (j - RM);
     });
@@ -271,7 +340,7 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
 }
 
 template <int RM, int RH>
-__global__ void __launch_bounds__(128) k_fast(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, 3) k_fast(const __grid_constant__ KParams p) {
   extern __shared__ __align__(16) float smem[];
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
@@ -279,9 +348,9 @@ __global__ void __launch_bounds__(128) k_fast(const __grid_constant__ KParams p)
   const FastLayout lay(L, RM, RH, NT, p.P);
   float *w_s = smem + lay.pack;
   float *s_s = smem + lay.s;
-  float *q_s = smem + lay.q;
-  float *ab_s = smem + lay.ab;
+  float4 *ab_s = reinterpret_cast<float4 *>(smem + lay.ab);
   float *red_s = smem + lay.red;
+  float *q_g = p.scratch + (size_t)blockIdx.x * fast_store_floats(L, RM, NT);
   const int npack = fast_pack_floats(L, RM, RH);
   for (int i = tid; i < npack; i += NT) w_s[i] = __ldg(p.pack + i);
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
@@ -297,14 +366,10 @@ __global__ void __launch_bounds__(128) k_fast(const __grid_constant__ KParams p)
       for (int j = tid; j < (NT / 32) * p.P; j += NT) red_s[j] = 0.0f;
     __syncthreads();
     float *red_w = red_s + (tid >> 5) * p.P;
-    if (T.kind == KIND_INT) {
-      if (p.grad && __ldg(p.nu + T.inst) == 0.0f)
-        fast_tile<RM, RH, 3>(p, T, w_s, s_s, q_s, ab_s, red_w);
-      else
-        fast_tile<RM, RH, 4>(p, T, w_s, s_s, q_s, ab_s, red_w);
-    } else {
-      fast_tile<RM, RH, 1>(p, T, w_s, s_s, q_s, ab_s, red_w);
-    }
+    if (T.kind == KIND_INT)
+      fast_tile<RM, RH, 4>(p, T, w_s, s_s, q_g, ab_s, red_w);
+    else
+      fast_tile<RM, RH, 1>(p, T, w_s, s_s, q_g, ab_s, red_w);
     if (p.grad) {
       __syncthreads();
       for (int j = tid; j < p.P; j += NT) {
@@ -325,14 +390,22 @@ cudaError_t launch_fast_t(const KParams &p, int grid_cap, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_fast<RM, RH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  int per_sm = 0, dev = 0, sms = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<RM, RH>, NT, bytes);
-  if (e != cudaSuccess) return e;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(grid_cap, std::max(1, per_sm) * sms));
-  k_fast<RM, RH><<<grid, NT, bytes, st>>>(p);
+  k_fast<RM, RH><<<std::max(1, grid_cap), NT, bytes, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int RM, int RH>
+int fast_ctas_per_sm_t(const KParams &p) {
+  const FastLayout lay(p.L, RM, RH, p.nt, p.P);
+  const size_t bytes = (size_t)lay.total * sizeof(float);
+  if (cudaFuncSetAttribute(k_fast<RM, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes) != cudaSuccess)
+    return 1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<RM, RH>, p.nt, bytes) !=
+      cudaSuccess)
+    return 1;
+  return std::max(1, per_sm);
 }
 
 }  // namespace lrnr

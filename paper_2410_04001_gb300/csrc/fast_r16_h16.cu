@@ -3,4 +3,5 @@
 
 namespace lrnr {
 template cudaError_t launch_fast_t<16, 16>(const KParams &, int, cudaStream_t);
+template int fast_ctas_per_sm_t<16, 16>(const KParams &);
 }  // namespace lrnr

@@ -255,14 +255,10 @@ __global__ void __launch_bounds__(NT) k_full_fp32(const __grid_constant__ KParam
       for (int j = tid; j < (NT / 32) * p.P; j += NT) red_s[j] = 0.0f;
     __syncthreads();
     float *red_w = red_s + (tid >> 5) * p.P;
-    if (T.kind == KIND_INT) {
-      if (p.grad && __ldg(p.nu + T.inst) == 0.0f)
-        full_tile<RM, NT, 3>(p, T, s_s, q_s, red_w);
-      else
-        full_tile<RM, NT, 4>(p, T, s_s, q_s, red_w);
-    } else {
+    if (T.kind == KIND_INT)
+      full_tile<RM, NT, 4>(p, T, s_s, q_s, red_w);
+    else
       full_tile<RM, NT, 1>(p, T, s_s, q_s, red_w);
-    }
     if (p.grad) {
       __syncthreads();
       for (int j = tid; j < p.P; j += NT) {

@@ -2,9 +2,9 @@
 // Eq. 2.1-2.2, Sec. 2.3), BF16 or split-BF16 operands with FP32 accumulation in
 // tensor memory.
 //
-// A CTA owns a tile of 128 collocation points; point p is thread p and TMEM lane p.
-// For every hidden layer the M-wide activation is produced and consumed in chunks
-// of NC = 32 columns, never stored whole (a width-chunked two-GEMM fusion):
+// A CTA owns a tile of 128 collocation points; point p is TMEM lane p.  For every
+// hidden layer the M-wide activation is produced and consumed in chunks of NC = 32
+// columns, never stored whole (a width-chunked two-GEMM fusion):
 //   forward   a_c  = (s * q_c) U_chunk^T            GEMM1  (M=128, N=NC, K=r)
 //             z_c  = tanh jet of a (+ bias)          epilogue, CUDA cores, FP32
 //             q'_c += z_c Vn_chunk                   GEMM2  (M=128, N=r, K=NC)
@@ -15,10 +15,15 @@
 // with one MMA per jet channel c (value, d/dt, d/dx, d2/dx2).  Split-BF16 keeps the
 // activations as hi + lo and the bases as hi + mid + lo (exact to 2^-24) and
 // accumulates five BF16 products per contraction.
-// The rank-r layer inputs q (FP32) are kept in a per-CTA global scratch area (it
-// stays in L2) for the reverse sweep.  Operands use the no-swizzle K-major
-// core-matrix layout; the host packs the bases chunk by chunk in that layout so a
-// chunk is one contiguous copy.  Every mbarrier wait is bounded.
+//
+// Eight warps: warps w and w+4 share TMEM lanes 32(w%4).. and split each chunk's
+// epilogue columns; warps 0-3 also do the per-point work.  Thread 0 issues the
+// MMAs and the bulk copies.  The bases are packed chunk by chunk in the operand
+// layout (no-swizzle K-major core matrices) so that one cp.async.bulk moves a
+// chunk; chunk j+1 is copied while chunk j is processed (two buffers when shared
+// memory allows).  The rank-r layer inputs q (FP32) are kept in a per-CTA global
+// scratch area (it stays in L2) for the reverse sweep.  Every mbarrier wait is
+// bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,32 +38,44 @@
 namespace lrnr {
 namespace {
 
-constexpr int TNT = 128;   // points per tile = threads = TMEM lanes
+constexpr int TNT = 128;   // points per tile = TMEM lanes
+constexpr int NTH = 256;   // threads: two per point (column halves of a chunk)
 constexpr int NC = 32;     // hidden-width chunk
+constexpr int HC = NC / 2; // columns per epilogue thread
 
+// Chunk block of the packed bases (bytes), three equal groups of PIECE bytes: the
+// hi pieces of Ub (NC x RM), Vb (NC x RM), Utb (RM x NC), Vtb (RM x NC) followed by
+// the chunk's biases (NC floats); then the mid pieces; then the lo pieces.
 template <int RM>
+struct Pk {
+  static constexpr int T = NC * RM * 2;
+  static constexpr int PIECE = 4 * T + 4 * NC;      // offset from a hi tile to its mid tile
+  static constexpr int HI = PIECE;                  // bytes needed by BF16
+  static constexpr int ALL = 3 * PIECE;             // bytes needed by split-BF16
+  static constexpr int CHUNK = ALL;
+};
+
+template <int RM, int PREC>
 struct TcLayout {
-  static constexpr int T = NC * RM * 2;            // bytes of one BF16 weight tile
-  static constexpr int CHUNK = 12 * T + 4 * NC;    // Ub, Vb, Utb, Vtb (hi, mid, lo) + bias
-  static constexpr int A1B = TNT * RM * 2;         // one (channel, part) rank-r operand
-  static constexpr int A24B = TNT * NC * 2;        // one (channel, part) width operand
+  static constexpr int PARTS = PREC == 3 ? 2 : 1;   // activation pieces
+  static constexpr int A1B = TNT * RM * 2;          // one (channel, piece) rank-r operand
+  static constexpr int A24B = TNT * NC * 2;         // one (channel, piece) width operand
+  static constexpr int BBYTES = PREC == 3 ? Pk<RM>::ALL : Pk<RM>::HI;
   static constexpr int OFF_A1 = 0;
-  static constexpr int OFF_A3 = OFF_A1 + 8 * A1B;
-  static constexpr int OFF_A24 = OFF_A3 + 8 * A1B;
-  static constexpr int OFF_B = OFF_A24 + 8 * A24B;
-  static constexpr int OFF_F = OFF_B + CHUNK;      // float area
-  // float area: s [(L+1)*RM], red [4][PL] (loss, dL/ds, output-bias dL/db), dbw [4][NC];
-  // then 2 mbarriers and the TMEM base address
-  static __host__ __device__ int floats(int L) { return (L + 1) * RM + 4 * (2 + (L + 1) * RM) + 4 * NC; }
-  static __host__ __device__ int bytes(int L) { return OFF_F + floats(L) * 4 + 64; }
+  static constexpr int OFF_A3 = OFF_A1 + 4 * PARTS * A1B;
+  static constexpr int OFF_A24 = OFF_A3 + 4 * PARTS * A1B;
+  static constexpr int OFF_B = OFF_A24 + 4 * PARTS * A24B;
+  static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
+  static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
+  static constexpr int OFF_F = OFF_B + NB * BSTRIDE;
+  // float area: s [(L+1)*RM], red [4][PL] (loss, dL/ds, output-bias dL/db), dbw [8][HC];
+  // then the mbarriers and the TMEM base address
+  static __host__ __device__ int floats(int L) { return (L + 1) * RM + 4 * (2 + (L + 1) * RM) + 8 * HC; }
+  static __host__ __device__ int bytes(int L) { return OFF_F + floats(L) * 4 + 128; }
 };
 
-struct Bars {
-  uint64_t *b1, *b2;
-  uint32_t ph1, ph2;
-};
-
-// All threads wait; false (and the device status set) if the wait timed out.
+// All threads wait for `bar` to complete the phase with parity `ph`; false (and the
+// device status set) if the wait timed out.
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, const KParams &p) {
   const bool ok = tc::mbar_wait(bar, ph, p.max_wait);
   ph ^= 1u;
@@ -68,18 +85,21 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, const KPar
   return all;
 }
 
-template <int RM>
-__device__ __forceinline__ void copy_chunk(const unsigned char *__restrict__ src, unsigned char *dst) {
-  constexpr int n16 = TcLayout<RM>::CHUNK / 16;
-  const uint4 *s = reinterpret_cast<const uint4 *>(src);
-  uint4 *d = reinterpret_cast<uint4 *>(dst);
-  for (int i = threadIdx.x; i < n16; i += TNT) d[i] = __ldg(s + i);
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
 }
 
 // Write a rank-r row (this thread's point) of channel c into a K-major operand.
 template <int RM, int PREC>
-__device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const float *v) {
-  constexpr int A1B = TcLayout<RM>::A1B;
+__device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const float *v, int row) {
+  using Lay = TcLayout<RM, PREC>;
 #pragma unroll
   for (int k0 = 0; k0 < RM; k0 += 8) {
     float w[8];
@@ -87,28 +107,28 @@ __device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const f
     for (int i = 0; i < 8; ++i) w[i] = v[k0 + i];
     uint4 hi, lo;
     tc::pack8_bf16(w, hi, lo);
-    const uint32_t off = tc::kmajor_off(threadIdx.x, k0, RM);
-    *reinterpret_cast<uint4 *>(base + (2 * c) * A1B + off) = hi;
-    if constexpr (PREC == 3) *reinterpret_cast<uint4 *>(base + (2 * c + 1) * A1B + off) = lo;
+    const uint32_t off = tc::kmajor_off(row, k0, RM);
+    *reinterpret_cast<uint4 *>(base + (Lay::PARTS * c) * Lay::A1B + off) = hi;
+    if constexpr (PREC == 3) *reinterpret_cast<uint4 *>(base + (2 * c + 1) * Lay::A1B + off) = lo;
   }
 }
 
 // D (+)= A B^T with A = Ah (+ Al) and B = Bh (+ Bm + Bl) in BF16 pieces.  BF16:
 // Ah Bh.  Split: Ah Bh + Ah Bm + Al Bh + Ah Bl + Al Bm; the dropped terms are below
 // 2^-25 relative, and the error left is that of the two-piece activation.
-// `b` is the shared address of the weight tile's first piece; pieces are T apart.
-template <int PREC>
+template <int RM, int PREC>
 __device__ __forceinline__ void mma_split(uint32_t d, uint32_t aHi, uint32_t aLo, uint32_t b,
-                                          uint32_t T, uint32_t sboA, uint32_t sboB,
-                                          uint32_t idesc, uint32_t acc) {
+                                          uint32_t sboA, uint32_t sboB, uint32_t idesc,
+                                          uint32_t acc) {
   const uint64_t ah = tc::sdesc(aHi, 128, sboA);
   tc::mma_bf16(d, ah, tc::sdesc(b, 128, sboB), idesc, acc);
   if constexpr (PREC == 3) {
+    constexpr uint32_t PC = Pk<RM>::PIECE;
     const uint64_t al = tc::sdesc(aLo, 128, sboA);
-    const uint64_t bm = tc::sdesc(b + T, 128, sboB);
+    const uint64_t bm = tc::sdesc(b + PC, 128, sboB);
     tc::mma_bf16(d, ah, bm, idesc, 1u);
     tc::mma_bf16(d, al, tc::sdesc(b, 128, sboB), idesc, 1u);
-    tc::mma_bf16(d, ah, tc::sdesc(b + 2 * T, 128, sboB), idesc, 1u);
+    tc::mma_bf16(d, ah, tc::sdesc(b + 2 * PC, 128, sboB), idesc, 1u);
     tc::mma_bf16(d, al, bm, idesc, 1u);
   }
 }
@@ -120,32 +140,43 @@ __device__ __forceinline__ void act_jet(float a0, float &z, float &d1, float &d2
   d2 = -2.0f * z * d1;
 }
 
+struct Ctl {
+  uint64_t *b1, *b2, *bb;   // GEMM barriers, B-buffer barriers [NB]
+  uint32_t ph1, ph2, phb[2];
+  int chunk_ctr;            // chunks consumed so far (selects the B buffer)
+};
+
 template <int RM, int PREC, int C>
 __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char *sm,
                         const unsigned char *__restrict__ pack, float *__restrict__ qst,
-                        uint32_t tb, Bars &bars, bool &dead) {
-  using Lay = TcLayout<RM>;
+                        uint32_t tb, Ctl &ctl, bool &dead) {
+  using Lay = TcLayout<RM, PREC>;
+  using PK = Pk<RM>;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (TNT - 1);       // point / TMEM lane
+  const int half = tid >> 7;             // column half of the epilogue
+  const bool lead = tid < TNT;           // threads doing the per-point work
   const int L = p.L, M = p.M;
   const int NCH = (M + NC - 1) / NC;
   unsigned char *sA1 = sm + Lay::OFF_A1;
   unsigned char *sA3 = sm + Lay::OFF_A3;
   unsigned char *sA24 = sm + Lay::OFF_A24;
-  unsigned char *sB = sm + Lay::OFF_B;
+  unsigned char *sB0 = sm + Lay::OFF_B;
   float *fa = reinterpret_cast<float *>(sm + Lay::OFF_F);
   const float *s_s = fa;
   const int PL = 2 + (L + 1) * RM;
-  float *red_w = fa + (L + 1) * RM + warp * PL;
+  float *red_w = fa + (L + 1) * RM + (warp & 3) * PL;
   float *dbw = fa + (L + 1) * RM + 4 * PL;
-  const float *bias_s = reinterpret_cast<const float *>(sB + 12 * Lay::T);
-  const float *tail = reinterpret_cast<const float *>(pack + (size_t)L * NCH * Lay::CHUNK);
+  const float *tail = reinterpret_cast<const float *>(pack + (size_t)L * NCH * PK::CHUNK);
   const float Uout = tail[2 * R1], bout = tail[2 * R1 + 1];
-  const uint32_t sA1u = tc::smem_u32(sA1), sA3u = tc::smem_u32(sA3), sA24u = tc::smem_u32(sA24),
-                 sBu = tc::smem_u32(sB);
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  const uint32_t D1 = tb, D3 = tb + C * NC, D24 = tb + 2 * 4 * NC;
+  const uint32_t sA1u = tc::smem_u32(sA1), sA3u = tc::smem_u32(sA3), sA24u = tc::smem_u32(sA24);
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t D1 = tb, D3 = tb + 4 * NC, D24 = tb + 8 * NC;
+  constexpr uint32_t ID_W = tc::idesc_bf16(128, NC);
+  constexpr uint32_t ID_R = tc::idesc_bf16(128, RM);
+  constexpr uint32_t SBO_R = RM * 16, SBO_W = NC * 16;
 
-  const PointIn pt = load_point(p, T, tid);
+  const PointIn pt = load_point(p, T, row);
   float q[C][RM];
   auto input_jet = [&]() {
 #pragma unroll
@@ -167,40 +198,53 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       float y[RM];
 #pragma unroll
       for (int k = 0; k < RM; ++k) y[k] = q[c][k] * s_s[l * RM + k];
-      put_rank_row<RM, PREC>(sA1, c, y);
+      put_rank_row<RM, PREC>(sA1, c, y, row);
     }
   };
-  auto read_rank = [&](uint32_t col0, float (&o)[C][RM]) {
+  auto read_rank = [&](float (&o)[C][RM]) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
 #pragma unroll
       for (int k0 = 0; k0 < RM; k0 += 16) {
         float v[16];
-        tc::tmem_ld16(col0 + lane_base + c * RM + k0, v);
+        tc::tmem_ld16(D24 + lane_base + c * RM + k0, v);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int i = 0; i < 16; ++i) o[c][k0 + i] = v[i];
       }
     }
   };
-  constexpr uint32_t ID_W = tc::idesc_bf16(128, NC);   // N = width chunk
-  constexpr uint32_t ID_R = tc::idesc_bf16(128, RM);   // N = rank
-  constexpr uint32_t SBO_R = RM * 16, SBO_W = NC * 16;
+  auto bbuf = [&](int n) { return sB0 + (n % Lay::NB) * Lay::BSTRIDE; };
+  // Stream the chunks of a layer through the B buffers: before chunk j, chunk j+1
+  // (or, with one buffer, chunk j itself) is requested.
+  auto fetch = [&](const unsigned char *lp, int j, int n) {
+    if (tid == 0)
+      bulk_copy(bbuf(n), lp + (size_t)j * PK::CHUNK, Lay::BBYTES, &ctl.bb[n % Lay::NB]);
+  };
+  auto wait_b = [&](int n) { return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], p); };
 
   // ---------------- forward
-  input_jet();
+  if (lead) input_jet();
   for (int l = 0; l < L && !dead; ++l) {
-    const unsigned char *lp = pack + (size_t)l * NCH * Lay::CHUNK;
-    if (p.grad && l > 0) {
+    const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
+    if (lead) {
+      if (p.grad && l > 0) {
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+        for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < RM; ++k) qst[(((l - 1) * 4 + c) * RM + k) * TNT + tid] = q[c][k];
+          for (int k = 0; k < RM; ++k) qst[(((l - 1) * 4 + c) * RM + k) * TNT + row] = q[c][k];
+      }
+      put_A1(l);
     }
-    put_A1(l);
+    const int n0 = ctl.chunk_ctr;
+    fetch(lp, 0, n0);
     for (int j = 0; j < NCH; ++j) {
-      if (j > 0 && !wait_bar(bars.b2, bars.ph2, p)) { dead = true; return; }
-      copy_chunk<RM>(lp + (size_t)j * Lay::CHUNK, sB);
+      const int n = n0 + j;
+      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }   // GEMM2(j-1) done
+      if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
+      if (!wait_b(n)) { dead = true; return; }
+      if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+      const uint32_t sB = tc::smem_u32(bbuf(n));
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -209,21 +253,21 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < RM / 16; ++kk)
-            mma_split<PREC>(D1 + c * NC, sA1u + (2 * c) * Lay::A1B + kk * 256,
-                            sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sBu + kk * 256, Lay::T,
-                            SBO_R, SBO_R, ID_W, kk > 0);
-        tc::mma_commit(bars.b1);
+            mma_split<RM, PREC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
+                                SBO_R, ID_W, kk > 0);
+        tc::mma_commit(ctl.b1);
       }
-      if (!wait_bar(bars.b1, bars.ph1, p)) { dead = true; return; }
-      // epilogue: tanh jets of the chunk, written as the A operand of GEMM2
-#pragma unroll
-      for (int c0 = 0; c0 < NC; c0 += 16) {
-        float a[C][16];
+      if (!wait_bar(ctl.b1, ctl.ph1, p)) { dead = true; return; }
+      const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
+      {
+        const int c0 = half * HC;
+        float a[C][HC];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld16(D1 + lane_base + c * NC + c0, a[c]);
         tc::tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < HC; ++i) {
           float z, d1, d2;
           act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
           if constexpr (C == 4) {
@@ -236,14 +280,14 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 #pragma unroll
         for (int c = 0; c < C; ++c)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < HC / 8; ++h) {
             float w8[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
             uint4 hi, lo;
             tc::pack8_bf16(w8, hi, lo);
-            const uint32_t off = tc::kmajor_off(tid, c0 + h * 8, NC);
-            *reinterpret_cast<uint4 *>(sA24 + (2 * c) * Lay::A24B + off) = hi;
+            const uint32_t off = tc::kmajor_off(row, c0 + h * 8, NC);
+            *reinterpret_cast<uint4 *>(sA24 + (Lay::PARTS * c) * Lay::A24B + off) = hi;
             if constexpr (PREC == 3) *reinterpret_cast<uint4 *>(sA24 + (2 * c + 1) * Lay::A24B + off) = lo;
           }
       }
@@ -256,28 +300,34 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < NC / 16; ++kk)
-            mma_split<PREC>(D24 + c * RM, sA24u + (2 * c) * Lay::A24B + kk * 256,
-                            sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sBu + 9 * Lay::T + kk * 256,
-                            Lay::T, SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
-        tc::mma_commit(bars.b2);
+            mma_split<RM, PREC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
+                                sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 3 * PK::T + kk * 256,
+                                SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+        tc::mma_commit(ctl.b2);
       }
     }
-    if (!wait_bar(bars.b2, bars.ph2, p)) { dead = true; return; }
-    read_rank(D24, q);
+    ctl.chunk_ctr = n0 + NCH;
+    if (!wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
+    if (lead) read_rank(q);
     tc::fence_before_sync();
   }
-  const float sL = s_s[L * RM];
   float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float sL = s_s[L * RM];
+  if (lead) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0];
-  u[0] += bout;
-  float ub[4], lpv;
-  if (!residual_and_seeds(p, T, pt, tid, u, ub, lpv)) return;
+    for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0];
+    u[0] += bout;
+  }
+  float ub[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lpv = 0.0f;
+  bool go = false;
+  if (lead) go = residual_and_seeds(p, T, pt, row, u, ub, lpv);
+  if (!__syncthreads_or(go)) return;      // evaluation mode: done
 
   // ---------------- reverse sweep
   const int DB0 = partial_db0(L, RM);
   float *prow = p.partial + (int64_t)tile * p.P;
-  {
+  float qb[C][RM];
+  if (lead) {
     // loss, dL/ds of the linear output layer, dL/db of the output bias
     const float ls = warp_sum(lpv);
     float dsL = 0.0f;
@@ -290,30 +340,38 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       red_w[1 + L * RM] += s0;
       red_w[PL - 1] += s1;
     }
-  }
-  float qb[C][RM];
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
+    for (int c = 0; c < C; ++c) {
 #pragma unroll
-    for (int k = 0; k < RM; ++k) qb[c][k] = 0.0f;
-    qb[c][0] = sL * Uout * ub[c];
+      for (int k = 0; k < RM; ++k) qb[c][k] = 0.0f;
+      qb[c][0] = sL * Uout * ub[c];
+    }
   }
   for (int l = L - 1; l >= 0 && !dead; --l) {
-    const unsigned char *lp = pack + (size_t)l * NCH * Lay::CHUNK;
-    if (l > 0) {
+    const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
+    if (lead) {
+      // qb first: it is dead once written, so q and qb are never live together
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int c = 0; c < C; ++c) put_rank_row<RM, PREC>(sA3, c, qb[c], row);
+      if (l > 0) {
 #pragma unroll
-        for (int k = 0; k < RM; ++k) q[c][k] = qst[(((l - 1) * 4 + c) * RM + k) * TNT + tid];
-    } else {
-      input_jet();
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int k = 0; k < RM; ++k) q[c][k] = qst[(((l - 1) * 4 + c) * RM + k) * TNT + row];
+      } else {
+        input_jet();
+      }
+      put_A1(l);
     }
-    put_A1(l);
-#pragma unroll
-    for (int c = 0; c < C; ++c) put_rank_row<RM, PREC>(sA3, c, qb[c]);
+    const int n0 = ctl.chunk_ctr;
+    fetch(lp, 0, n0);
     for (int j = 0; j < NCH; ++j) {
-      if (j > 0 && !wait_bar(bars.b2, bars.ph2, p)) { dead = true; return; }
-      copy_chunk<RM>(lp + (size_t)j * Lay::CHUNK, sB);
+      const int n = n0 + j;
+      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
+      if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
+      if (!wait_b(n)) { dead = true; return; }
+      if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+      const uint32_t sB = tc::smem_u32(bbuf(n));
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -322,18 +380,20 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < RM / 16; ++kk) {
-            mma_split<PREC>(D1 + c * NC, sA1u + (2 * c) * Lay::A1B + kk * 256,
-                            sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sBu + kk * 256, Lay::T,
-                            SBO_R, SBO_R, ID_W, kk > 0);
-            mma_split<PREC>(D3 + c * NC, sA3u + (2 * c) * Lay::A1B + kk * 256,
-                            sA3u + (2 * c + 1) * Lay::A1B + kk * 256, sBu + 3 * Lay::T + kk * 256,
-                            Lay::T, SBO_R, SBO_R, ID_W, kk > 0);
+            mma_split<RM, PREC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
+                                SBO_R, ID_W, kk > 0);
+            mma_split<RM, PREC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                sA3u + (2 * c + 1) * Lay::A1B + kk * 256, sB + PK::T + kk * 256,
+                                SBO_R, SBO_R, ID_W, kk > 0);
           }
-        tc::mma_commit(bars.b1);
+        tc::mma_commit(ctl.b1);
       }
-      if (!wait_bar(bars.b1, bars.ph1, p)) { dead = true; return; }
+      if (!wait_bar(ctl.b1, ctl.ph1, p)) { dead = true; return; }
+      const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
 #pragma unroll
-      for (int c0 = 0; c0 < NC; c0 += 8) {
+      for (int h8 = 0; h8 < HC / 8; ++h8) {
+        const int c0 = half * HC + h8 * 8;
         float a[C][8], wb[C][8];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -360,15 +420,15 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c) {
           uint4 hi, lo;
           tc::pack8_bf16(wb[c], hi, lo);
-          const uint32_t off = tc::kmajor_off(tid, c0, NC);
-          *reinterpret_cast<uint4 *>(sA24 + (2 * c) * Lay::A24B + off) = hi;
+          const uint32_t off = tc::kmajor_off(row, c0, NC);
+          *reinterpret_cast<uint4 *>(sA24 + (Lay::PARTS * c) * Lay::A24B + off) = hi;
           if constexpr (PREC == 3) *reinterpret_cast<uint4 *>(sA24 + (2 * c + 1) * Lay::A24B + off) = lo;
         }
         float g8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) g8[i] = wb[0][i];
         const float r = warp_reduce_scatter<8>(g8);
-        if ((lane & 3) == 0) dbw[warp * NC + c0 + (lane >> 2)] = r;
+        if ((lane & 3) == 0) dbw[warp * HC + h8 * 8 + (lane >> 2)] = r;
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
@@ -379,49 +439,61 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < NC / 16; ++kk)
-            mma_split<PREC>(D24 + c * RM, sA24u + (2 * c) * Lay::A24B + kk * 256,
-                            sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sBu + 6 * Lay::T + kk * 256,
-                            Lay::T, SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
-        tc::mma_commit(bars.b2);
+            mma_split<RM, PREC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
+                                sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 2 * PK::T + kk * 256,
+                                SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+        tc::mma_commit(ctl.b2);
       }
       if (tid < NC) {
+        // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
+        const int h = tid / HC, cc = tid % HC;
+        const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
+                        dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
         const int col = j * NC + tid;
-        const float v = dbw[tid] + dbw[NC + tid] + dbw[2 * NC + tid] + dbw[3 * NC + tid];
         if (col < M) prow[DB0 + l * M + col] = v;
       }
     }
-    if (!wait_bar(bars.b2, bars.ph2, p)) { dead = true; return; }
-    float pb[C][RM];
-    read_rank(D24, pb);
-    tc::fence_before_sync();
-    if (l > 0) {
+    ctl.chunk_ctr = n0 + NCH;
+    if (!wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
+    if (lead) {
+      float pb[C][RM];
+      read_rank(pb);
+      // dL/ds^l = sum_c pbar_c * q_c, reading q element by element
+      float g[RM];
+#pragma unroll
+      for (int k = 0; k < RM; ++k) {
+        float d = 0.0f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          float qv;
+          if (l > 0) {
+            qv = qst[(((l - 1) * 4 + c) * RM + k) * TNT + row];
+          } else {
+            qv = 0.0f;
+            if (k < R1) {
+              if (c == 0) qv = tail[k] * pt.x + tail[R1 + k] * pt.t;
+              else if (c == 1) qv = tail[R1 + k];
+              else if (c == 2) qv = tail[k];
+            }
+          }
+          d = fmaf(pb[c][k], qv, d);
+        }
+        g[k] = d;
+      }
+      warp_accumulate<RM>(g, red_w, [&](int jj) { return 1 + l * RM + jj; });
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < RM; ++k) q[c][k] = qst[(((l - 1) * 4 + c) * RM + k) * TNT + tid];
-    } else {
-      input_jet();
+        for (int k = 0; k < RM; ++k) qb[c][k] = pb[c][k] * s_s[l * RM + k];
     }
-    float g[RM];
-#pragma unroll
-    for (int k = 0; k < RM; ++k) {
-      float d = 0.0f;
-#pragma unroll
-      for (int c = 0; c < C; ++c) d = fmaf(pb[c][k], q[c][k], d);
-      g[k] = d;
-    }
-    warp_accumulate<RM>(g, red_w, [&](int jj) { return 1 + l * RM + jj; });
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < RM; ++k) qb[c][k] = pb[c][k] * s_s[l * RM + k];
+    tc::fence_before_sync();
   }
 }
 
 template <int RM, int PREC>
-__global__ void __launch_bounds__(TNT, 1) k_full_tc(const __grid_constant__ KParams p,
+__global__ void __launch_bounds__(NTH, 1) k_full_tc(const __grid_constant__ KParams p,
                                                   const unsigned char *__restrict__ pack) {
-  using Lay = TcLayout<RM>;
+  using Lay = TcLayout<RM, PREC>;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x;
   const int L = p.L;
@@ -429,42 +501,39 @@ __global__ void __launch_bounds__(TNT, 1) k_full_tc(const __grid_constant__ KPar
   float *s_s = fa;
   const int PL = 2 + (L + 1) * RM;
   float *red_s = fa + (L + 1) * RM;
-  float *dbw = red_s + 4 * PL;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((Lay::OFF_F + Lay::floats(L) * 4 + 15) & ~15));
-  uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 2);
+  uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
   if (tid < 32) tc::tmem_alloc(tbase, 512);
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
     tc::fence_mbar_init();
   }
-  for (int i = tid; i < 4 * NC; i += TNT) dbw[i] = 0.0f;
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tb = *tbase;
-  Bars bars{&bar[0], &bar[1], 0u, 0u};
+  Ctl ctl{&bar[0], &bar[1], &bar[2], 0u, 0u, {0u, 0u}, 0};
   bool dead = false;
   float *qst = p.scratch + (size_t)blockIdx.x * (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * TNT;
   const int ntiles = __ldg(p.tile_off + p.n_inst);
   for (int tile = blockIdx.x; tile < ntiles && !dead; tile += gridDim.x) {
     const Tile T = decode_tile(p, tile);
     __syncthreads();
-    for (int j = tid; j < (L + 1) * RM; j += TNT) {
+    for (int j = tid; j < (L + 1) * RM; j += NTH) {
       const int l = j / RM, k = j % RM;
       s_s[j] = (k < p.r[l]) ? __ldg(p.s + (int64_t)T.inst * p.sum_r + p.roff[l] + k) : 0.0f;
     }
-    for (int j = tid; j < 4 * PL; j += TNT) red_s[j] = 0.0f;
+    for (int j = tid; j < 4 * PL; j += NTH) red_s[j] = 0.0f;
     __syncthreads();
     if (T.kind == KIND_INT)
-      tc_tile<RM, PREC, 4>(p, T, tile, sm, pack, qst, tb, bars, dead);
+      tc_tile<RM, PREC, 4>(p, T, tile, sm, pack, qst, tb, ctl, dead);
     else
-      tc_tile<RM, PREC, 1>(p, T, tile, sm, pack, qst, tb, bars, dead);
+      tc_tile<RM, PREC, 1>(p, T, tile, sm, pack, qst, tb, ctl, dead);
     if (dead) break;
     if (p.grad) {
       __syncthreads();
-      for (int j = tid; j < PL; j += TNT) {
+      for (int j = tid; j < PL; j += NTH) {
         const float acc = red_s[j] + red_s[PL + j] + red_s[2 * PL + j] + red_s[3 * PL + j];
         if (j == 0 && !isfinite(acc)) set_status(p.status, DEV_NONFINITE);
         // entries 0 .. PL-2 are the loss and dL/ds; the last is the output-bias dL/db
@@ -474,9 +543,10 @@ __global__ void __launch_bounds__(TNT, 1) k_full_tc(const __grid_constant__ KPar
     }
   }
   if (dead) {
-    // give in-flight tensor-core work a bounded chance to finish before freeing TMEM
-    tc::mbar_wait(bars.b1, bars.ph1, p.max_wait);
-    tc::mbar_wait(bars.b2, bars.ph2, p.max_wait);
+    // give in-flight tensor-core work and copies a bounded chance to finish
+    tc::mbar_wait(ctl.b1, ctl.ph1, p.max_wait);
+    tc::mbar_wait(ctl.b2, ctl.ph2, p.max_wait);
+    for (int b = 0; b < Lay::NB; ++b) tc::mbar_wait(&ctl.bb[b], ctl.phb[b], p.max_wait);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -501,7 +571,7 @@ float bf16_val(uint16_t b) {
 
 template <int RM, int PREC>
 cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaStream_t st) {
-  using Lay = TcLayout<RM>;
+  using Lay = TcLayout<RM, PREC>;
   const size_t bytes = (size_t)Lay::bytes(p.L);
   cudaError_t e = cudaFuncSetAttribute(k_full_tc<RM, PREC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -510,7 +580,7 @@ cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaSt
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min(grid_cap, sms));
-  k_full_tc<RM, PREC><<<grid, TNT, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
+  k_full_tc<RM, PREC><<<grid, NTH, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
   return cudaGetLastError();
 }
 
@@ -519,7 +589,7 @@ cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaSt
 int full_tc_supported(int L, int M, int RM) {
   if (RM != 16 && RM != 32) return 0;
   if (L < 1 || M < 1) return 0;
-  const int bytes = RM == 16 ? TcLayout<16>::bytes(L) : TcLayout<32>::bytes(L);
+  const int bytes = RM == 16 ? TcLayout<16, 3>::bytes(L) : TcLayout<32, 3>::bytes(L);
   return bytes <= 227 * 1024 ? 1 : 0;
 }
 
@@ -531,20 +601,22 @@ size_t full_tc_scratch_floats(int L, int RM, int grid) {
 
 size_t full_tc_pack_bytes(int L, int M, int RM) {
   const int NCH = (M + NC - 1) / NC;
-  const size_t chunk = RM == 16 ? TcLayout<16>::CHUNK : TcLayout<32>::CHUNK;
+  const size_t chunk = RM == 16 ? Pk<16>::CHUNK : Pk<32>::CHUNK;
   return (size_t)L * NCH * chunk + 64;
 }
 
 // Pack the bases for the tensor-core kernel: per hidden layer l and chunk j of NC
-// rows, the K-major BF16 tiles (three pieces each) of U^l (rows i, K = rank in),
-// V^{l+1} (rows i, K = rank out), U^l^T and V^{l+1}^T (rows = rank, K = chunk),
-// then the chunk's biases; ranks are zero-padded to RM and rows to a multiple of NC.
+// rows, the K-major BF16 tiles of U^l (rows i, K = rank in), V^{l+1} (rows i,
+// K = rank out), U^l^T and V^{l+1}^T (rows = rank, K = chunk) -- first their hi
+// pieces and the chunk's biases, then the mid pieces, then the lo pieces; ranks
+// are zero-padded to RM and rows to a multiple of NC.
 void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &U,
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
                   const int *r, std::vector<unsigned char> &out) {
   const int NCH = (M + NC - 1) / NC;
   const int T = NC * RM * 2;
-  const int CHUNK = 12 * T + 4 * NC;
+  const int PIECE = 4 * T + 4 * NC;
+  const int CHUNK = 3 * PIECE;
   out.assign(full_tc_pack_bytes(L, M, RM), 0);
   // three BF16 pieces: hi = rn(x), mid = rn(x - hi), lo = rn(x - hi - mid)
   auto put = [&](size_t base, int part, double x, int row, int k, int K) {
@@ -553,7 +625,7 @@ void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &
     const uint16_t m = bf16_bits((float)r1);
     const uint16_t lo = bf16_bits((float)(r1 - (double)bf16_val(m)));
     const uint16_t v = part == 0 ? h : (part == 1 ? m : lo);
-    std::memcpy(&out[base + part * T + tc::kmajor_off(row, k, K)], &v, 2);
+    std::memcpy(&out[base + part * PIECE + tc::kmajor_off(row, k, K)], &v, 2);
   };
   for (int l = 0; l < L; ++l) {
     const int rin = r[l], rout = r[l + 1];
@@ -566,16 +638,16 @@ void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &
           for (int k = 0; k < rin; ++k) {
             const double u = U[l][(size_t)i * rin + k];
             put(cb + 0 * T, part, u, ii, k, RM);       // Ub
-            put(cb + 6 * T, part, u, k, ii, NC);       // Utb
+            put(cb + 2 * T, part, u, k, ii, NC);       // Utb
           }
           for (int k = 0; k < rout; ++k) {
             const double v = V[l + 1][(size_t)i * rout + k];
-            put(cb + 3 * T, part, v, ii, k, RM);       // Vb
-            put(cb + 9 * T, part, v, k, ii, NC);       // Vtb
+            put(cb + 1 * T, part, v, ii, k, RM);       // Vb
+            put(cb + 3 * T, part, v, k, ii, NC);       // Vtb
           }
         }
         const float bv = (float)b[l][i];
-        std::memcpy(&out[cb + 12 * T + 4 * ii], &bv, 4);
+        std::memcpy(&out[cb + 4 * T + 4 * ii], &bv, 4);
       }
     }
   }

@@ -30,6 +30,7 @@ struct KParams {
   int L, M, n_inst;
   int RM;                      // padded hidden rank used by the packs
   int RH;                      // padded EIM row count (fast form)
+  int rh[LMAX];                // EIM rows kept per hidden layer (fast form)
   int r[LMAX + 1];             // ranks of the L+1 weight layers
   int roff[LMAX + 2];          // offsets of each layer's s in an instance vector
   int sum_r;
@@ -162,11 +163,14 @@ constexpr int kSmemBudget = 220 * 1024;   // dynamic shared memory a tile kernel
 
 size_t fast_smem_bytes(int L, int RM, int RH, int NT, int P);
 int fast_choose_nt(int L, int RM, int RH, int P);
+int fast_ctas_per_sm(const KParams &p);                 // resident CTAs of k_fast per SM
+size_t fast_scratch_floats(int L, int RM, int NT, int grid);  // layer-input store
 size_t full_fp32_smem_bytes(int L, int RM, int NT, int P);
 int full_fp32_choose_nt(int L, int RM, int P);
 cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_t st);
-// grid_cap bounds the persistent grid (never more CTAs than tiles).
-cudaError_t launch_fast(const KParams &p, int grid_cap, cudaStream_t st);
+// grid_cap bounds the persistent grid (never more CTAs than tiles); the FastLRNR
+// kernel is launched with exactly `grid` CTAs (its scratch is sized for them).
+cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_fp32(const KParams &p, int grid_cap, cudaStream_t st);
 cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int grid_cap,
                            cudaStream_t st);

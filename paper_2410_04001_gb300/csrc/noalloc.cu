@@ -9,6 +9,7 @@
 // of the model's workspace.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "lrnr_internal.cuh"
@@ -22,8 +23,8 @@ int64_t noalloc_max_tiles(const lrnr_batch *bt, int nt);
 
 namespace {
 
-// 8 MiB of scratch per device, allocated with the module and kept until exit.
-constexpr size_t kScratchBytes = size_t(8) << 20;
+// 32 MiB of scratch per device, allocated with the module and kept until exit.
+constexpr size_t kScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -62,12 +63,17 @@ extern "C" lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batc
   int sum_m = 0, dev = 0;
   lrnr_status rc = noalloc_fast_params(m, bt, loss, w, p, &rows, &sum_m, &dev);
   if (rc != LRNR_OK) return rc;
-  // capacity: tile offsets, then one partial row per tile
+  // capacity: tile offsets, one partial row per tile, then the layer-input store of
+  // as many CTAs as the rest of the array holds (at least one)
   const int64_t tiles = noalloc_max_tiles(bt, p.nt);
   const size_t off_part = round256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));
   if (tiles < 0 || off_part > kScratchBytes ||
       (size_t)tiles * (size_t)p.P * sizeof(float) > kScratchBytes - off_part)
     return LRNR_ETOOBIG;
+  const size_t off_store = off_part + round256((size_t)tiles * (size_t)p.P * sizeof(float));
+  const size_t per_cta = fast_scratch_floats(p.L, p.RM, p.nt, 1) * sizeof(float);
+  if (off_store > kScratchBytes || (kScratchBytes - off_store) / per_cta < 1) return LRNR_ETOOBIG;
+  int sms = 1;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess) return LRNR_ECUDA;
   if (cur != dev && cudaSetDevice(dev) != cudaSuccess) return LRNR_ECUDA;
@@ -76,8 +82,12 @@ extern "C" lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batc
   if (rc == LRNR_OK) {
     p.tile_off = static_cast<int32_t *>(base);
     p.partial = reinterpret_cast<float *>(static_cast<unsigned char *>(base) + off_part);
+    p.scratch = reinterpret_cast<float *>(static_cast<unsigned char *>(base) + off_store);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int grid_cap = (int)tiles;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t fit = (int64_t)((kScratchBytes - off_store) / per_cta);
+    const int grid_cap = (int)std::min<int64_t>(
+        std::min<int64_t>(tiles, (int64_t)fast_ctas_per_sm(p) * sms), fit);
     cudaError_t e = launch_tile_offsets(p, static_cast<int32_t *>(base), st);
     if (e == cudaSuccess) e = launch_fast(p, grid_cap, st);
     if (e == cudaSuccess && dL_db)

@@ -41,6 +41,23 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *io, const 
   if (tid == 1023) tile_off[n_inst] = sums[1023];
 }
 
+// Sum of column j over the rows t0 + g, t0 + g + 32, ... < t1 of the partial
+// matrix, with four independent accumulators so that several loads are in flight;
+// the order of the additions is fixed.
+__device__ __forceinline__ float column_sum(const float *__restrict__ part, int P, int j, int t0,
+                                            int t1, int g) {
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+  int t = t0 + g;
+  for (; t + 96 < t1; t += 128) {
+    a0 += __ldg(part + (int64_t)t * P + j);
+    a1 += __ldg(part + (int64_t)(t + 32) * P + j);
+    a2 += __ldg(part + (int64_t)(t + 64) * P + j);
+    a3 += __ldg(part + (int64_t)(t + 96) * P + j);
+  }
+  for (; t < t1; t += 32) a0 += __ldg(part + (int64_t)t * P + j);
+  return (a0 + a1) + (a2 + a3);
+}
+
 struct RedArgs {
   const float *partial;
   const int32_t *tile_off;
@@ -83,7 +100,7 @@ __global__ void __launch_bounds__(1024) k_reduce(const __grid_constant__ RedArgs
   const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
   float acc = 0.0f;
   if (j < a.n_needed)
-    for (int t = t0 + threadIdx.y; t < t1; t += 32) acc += a.partial[(int64_t)t * a.P + j];
+    acc = column_sum(a.partial, a.P, j, t0, t1, threadIdx.y);
   sh[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
   if (threadIdx.y == 0 && j < a.n_needed) {
@@ -118,7 +135,7 @@ __global__ void __launch_bounds__(1024) k_reduce_adam(const __grid_constant__ Ad
     const int j = c0 + tx;
     float acc = 0.0f;
     if (j < DB0)
-      for (int t = t0 + ty; t < t1; t += 32) acc += a.partial[(int64_t)t * a.P + j];
+      acc = column_sum(a.partial, a.P, j, t0, t1, ty);
     sh[ty][tx] = acc;
     __syncthreads();
     if (ty == 0 && j < DB0) {

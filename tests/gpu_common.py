@@ -71,3 +71,42 @@ def bc_err(got, Bbc, model, bt, form):
             scale += float(np.sum(u0[:, 0] ** 2))
     d = np.linalg.norm(np.asarray(got, np.float64) - Bbc)
     return d / np.sqrt(scale) if scale > 0 else d
+
+
+def jet_magnitudes(net, s, x, t):
+    """Rounding scale of each output jet channel: the forward pass with every sum
+    replaced by the root of the sum of its squared terms (sqrt(V^2^T z^2), ...) and
+    the jet rules applied to those scales.  The rounding error of a long sum of terms
+    of mixed sign grows like eps times this root-sum-square (not like eps times the
+    result), so this is the scale against which the error of an ill-conditioned
+    channel -- a small result of large cancelling sums, as u_xx is in deep networks
+    with these weights -- is measured."""
+    x = np.asarray(x, np.float64)
+    t = np.asarray(t, np.float64)
+    off = np.cumsum([0] + list(net.r))
+    Zm = np.zeros((x.shape[0], 4, 2))
+    Zm[:, 0, 0], Zm[:, 0, 1] = np.abs(x), np.abs(t)
+    Zm[:, 1, 1] = 1.0
+    Zm[:, 2, 0] = 1.0
+    Zv = lrnr64.input_jets(x, t)
+    for l in range(net.L + 1):
+        sl = np.asarray(s[off[l]:off[l + 1]], np.float64)
+        qm = np.sqrt((Zm ** 2) @ (net.V[l] ** 2)) * np.abs(sl)
+        am = np.sqrt((qm ** 2) @ (net.U[l] ** 2).T)
+        am[:, 0] = np.sqrt(am[:, 0] ** 2 + net.b[l] ** 2)
+        av = ((Zv @ net.V[l]) * sl) @ net.U[l].T
+        av[:, 0] += net.b[l]
+        if l == net.L:
+            return am[:, :, 0]
+        z, d1, d2, _ = lrnr64.tanh_derivs(av[:, 0])
+        Zv, _ = lrnr64.act_jets(av)
+        Zm = np.empty_like(am)
+        Zm[:, 0] = np.abs(z)
+        Zm[:, 1] = np.abs(d1) * am[:, 1]
+        Zm[:, 2] = np.abs(d1) * am[:, 2]
+        Zm[:, 3] = np.sqrt((d2 * am[:, 2] ** 2) ** 2 + (d1 * am[:, 3]) ** 2)
+
+
+def jet_err(got, ref, mag):
+    """Normwise error of one jet channel measured against its magnitude."""
+    return float(np.linalg.norm(np.asarray(got, np.float64) - ref) / np.linalg.norm(mag))
