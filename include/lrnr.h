@@ -218,6 +218,16 @@ lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batch *bt, lrnr
  * before capturing a CUDA graph. */
 lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst);
 
+/* lrnr_set_tuning -- override the launch shape used for (form, prec): points per
+ * tile `nt` (32, 64 or 128; 0 = automatic) and a cap on resident CTAs per SM
+ * `ctas_per_sm` (1..8; 0 = automatic).  Shapes that do not fit the kernel's
+ * shared memory fall back to the automatic choice.  Results change only by
+ * rounding (tiles regroup the partial sums).  Set by the autotuner
+ * (paper_2410_04001_gb300/autotune.py), which times the candidates on the
+ * caller's batch.  The tensor-core form has a fixed shape (128 points, 1 CTA). */
+lrnr_status lrnr_set_tuning(lrnr_model *m, lrnr_form form, lrnr_precision prec, int nt,
+                            int ctas_per_sm);
+
 /* lrnr_model_info -- host outputs (any may be NULL): L, M, sum_r, sum_m and
  * whether every hidden layer has reduced bases (fast_ready). */
 lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int *sum_m,

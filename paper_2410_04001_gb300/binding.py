@@ -61,6 +61,7 @@ _SIGS = {
     "lrnr_residual_grad_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "lrnr_reserve": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "lrnr_model_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lrnr_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lrnr_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "lrnr_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "lrnr_last_device_status": (ctypes.c_int, [_P]),
@@ -163,6 +164,12 @@ def lrnr_model_info(model: Model) -> dict:
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib().lrnr_model_info(model.handle, *[ctypes.byref(x) for x in v]), "lrnr_model_info")
     return dict(zip(("L", "M", "sum_r", "sum_m", "fast_ready"), [x.value for x in v]))
+
+
+def lrnr_set_tuning(model: Model, form: str, prec: str, nt: int = 0, ctas_per_sm: int = 0):
+    """Override the launch shape for (form, prec); 0 = automatic."""
+    _check(lib().lrnr_set_tuning(model.handle, _FORM[form], _PREC[prec], int(nt), int(ctas_per_sm)),
+           "lrnr_set_tuning")
 
 
 def lrnr_timing(model: Model, enable: bool = True):

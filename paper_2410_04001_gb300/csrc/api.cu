@@ -61,6 +61,12 @@ struct lrnr_model {
   std::vector<cudaEvent_t> ev_start, ev_stop;
   size_t ev_used = 0;
   std::vector<cudaEvent_t> cap_start, cap_stop;
+  // launch-shape overrides per (form, precision): points per tile, CTAs per SM cap
+  int tune_nt[2][4] = {{0}};
+  int tune_cta[2][4] = {{0}};
+  // per-instance tickets of the two-level Adam reduction (zero between calls)
+  int *adam_cnt = nullptr;
+  int adam_cnt_n = 0;
 };
 
 namespace {
@@ -184,10 +190,11 @@ struct Pass {
   KParams p;
   int grid_cap;
   int nb_entries;     // partial entries beyond dL/ds (dL/db block)
+  float *gsum = nullptr;   // Adam group rows (spinprop_step)
 };
 
 lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lrnr_batch *bt,
-                    bool grad, const float *s, cudaStream_t st, Pass &ps) {
+                    bool grad, const float *s, cudaStream_t st, Pass &ps, bool adam = false) {
   lrnr_status rc = check_batch(m, bt);
   if (rc != LRNR_OK) return rc;
   if (!s) return LRNR_EINVAL;
@@ -212,8 +219,15 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     p.RH = m->fRH;
     p.pack = m->fast_pack;
     for (int l = 0; l < m->L; ++l) p.rh[l] = m->rhat[l];
+    p.fused_tiles = bt->n_inst <= 4096 ? 1 : 0;   // the kernel computes its tile offsets
     p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
     if (!p.nt) return LRNR_ENOTSUP;
+    {
+      const int tn = m->tune_nt[LRNR_FAST][prec];
+      if (tn && fast_smem_bytes(m->L, p.RM, p.RH, tn, partial_len(m->L, p.RM, m->L * p.RH + 1)) <=
+                    (size_t)kSmemBudget)
+        p.nt = tn;
+    }
     ps.nb_entries = m->L * p.RH + 1;
   } else if (form == LRNR_FULL) {
     p.RM = m->RM;
@@ -222,6 +236,11 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
       p.pack = m->full_pack;
       p.nt = full_fp32_choose_nt(m->L, p.RM, partial_len(m->L, p.RM, m->L * m->M + 1));
       if (!p.nt) return LRNR_ENOTSUP;
+      const int tn = m->tune_nt[LRNR_FULL][prec];
+      if ((tn == 32 || tn == 64) &&
+          full_fp32_smem_bytes(m->L, p.RM, tn, partial_len(m->L, p.RM, m->L * m->M + 1)) <=
+              (size_t)kSmemBudget)
+        p.nt = tn;
     } else if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
       p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
       if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM)) return LRNR_ENOTSUP;
@@ -245,16 +264,30 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     scr_bytes = full_tc_scratch_floats(m->L, p.RM, ps.grid_cap) * sizeof(float);
   } else if (form == LRNR_FAST) {
     // the FastLRNR kernel keeps layer inputs in a per-CTA scratch: size the grid first
-    ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)fast_ctas_per_sm(p) * m->num_sms);
+    // 255-register build (2 CTAs/SM) unless the tuning asks for 3 CTAs per SM
+    p.fast_regs = m->tune_cta[LRNR_FAST][prec] >= 3 ? 3 : 2;
+    int per_sm = fast_ctas_per_sm(p);
+    if (m->tune_cta[LRNR_FAST][prec] > 0) per_sm = std::min(per_sm, m->tune_cta[LRNR_FAST][prec]);
+    ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
     if (grad) scr_bytes = fast_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap) * sizeof(float);
+  } else {
+    // the FP32 full-width kernel also keeps layer inputs in a per-CTA scratch
+    int per_sm = full_fp32_ctas_per_sm(p);
+    if (m->tune_cta[LRNR_FULL][prec] > 0) per_sm = std::min(per_sm, m->tune_cta[LRNR_FULL][prec]);
+    ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
+    if (grad) scr_bytes = full_fp32_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap) * sizeof(float);
   }
   const size_t off_part = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));
   const size_t part_bytes = grad ? align256((size_t)tiles * p.P * sizeof(float)) : 0;
-  rc = ensure_ws(m, off_part + part_bytes + scr_bytes, st);
+  const size_t scr_al = align256(scr_bytes);
+  const size_t adam_bytes = adam ? adam_group_floats(bt->n_inst, m->L, p.RM) * sizeof(float) : 0;
+  rc = ensure_ws(m, off_part + part_bytes + scr_al + adam_bytes, st);
   if (rc != LRNR_OK) return rc;
   p.tile_off = reinterpret_cast<int32_t *>(m->ws);
   p.partial = reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part);
   p.scratch = scr_bytes ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes) : nullptr;
+  ps.gsum = adam ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes + scr_al)
+                 : nullptr;
   p.max_wait = 1u << 20;
   p.loss = LRNR_LOSS_MSE;
   p.w[0] = p.w[1] = p.w[2] = 1.0f;
@@ -264,7 +297,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
 lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &ps,
                      cudaStream_t st) {
   KParams &p = ps.p;
-  CK(launch_tile_offsets(p, const_cast<int32_t *>(p.tile_off), st));
+  if (!p.fused_tiles) CK(launch_tile_offsets(p, const_cast<int32_t *>(p.tile_off), st));
   cudaEvent_t e1 = nullptr, e2 = nullptr;
   const bool cap = m->timing && capturing(st);
   if (cap) {
@@ -588,8 +621,20 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec, co
   DeviceGuard g(m->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Pass ps;
-  lrnr_status rc = prepare(m, form, prec, bt, true, s_inout, st, ps);
+  lrnr_status rc = prepare(m, form, prec, bt, true, s_inout, st, ps, true);
   if (rc != LRNR_OK) return rc;
+  if (m->adam_cnt_n < bt->n_inst) {
+    if (capturing(st)) return LRNR_ENOTREADY;
+    if (m->adam_cnt) {
+      CK(cudaStreamSynchronize(st));
+      CK(cudaFree(m->adam_cnt));
+      m->adam_cnt = nullptr;
+      m->adam_cnt_n = 0;
+    }
+    CK(cudaMalloc(&m->adam_cnt, sizeof(int) * (size_t)bt->n_inst));
+    CK(cudaMemset(m->adam_cnt, 0, sizeof(int) * (size_t)bt->n_inst));
+    m->adam_cnt_n = bt->n_inst;
+  }
   ps.p.loss = loss;
   if (w) { ps.p.w[0] = w[0]; ps.p.w[1] = w[1]; ps.p.w[2] = w[2]; }
   ps.p.step = step;
@@ -597,7 +642,7 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec, co
     rc = run_main(m, form, prec, ps, st);
     if (rc != LRNR_OK) return rc;
     CK(launch_reduce_adam(ps.p, s_inout, adam_m, adam_v, step, lr, beta1, beta2, eps, lambda_loc,
-                          s_anchor, loss_out, st));
+                          s_anchor, loss_out, ps.gsum, m->adam_cnt, st));
   }
   return LRNR_OK;
 }
@@ -660,11 +705,33 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   int Pmax = partial_len(m->L, m->RM, m->L * m->M + 1);
   Pmax = std::max(Pmax, partial_len(m->L, RMAX, m->L * RHMAX + 1));
   // per-CTA layer-input stores (tensor-core and FastLRNR kernels): at most 4 CTAs per SM
-  const size_t store = std::max(full_tc_scratch_floats(m->L, RMAX, m->num_sms),
-                                fast_scratch_floats(m->L, RMAX, 128, 4 * m->num_sms));
+  const size_t store = std::max(std::max(full_tc_scratch_floats(m->L, RMAX, m->num_sms),
+                                         fast_scratch_floats(m->L, RMAX, 128, 4 * m->num_sms)),
+                                full_fp32_scratch_floats(m->L, RMAX, 64, 8 * m->num_sms));
   const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) +
-                      align256((size_t)tiles * Pmax * sizeof(float)) + store * sizeof(float);
+                      align256((size_t)tiles * Pmax * sizeof(float)) +
+                      align256(store * sizeof(float)) +
+                      adam_group_floats(max_inst, m->L, RMAX) * sizeof(float);
+  if (m->adam_cnt_n < max_inst) {
+    if (m->adam_cnt) CK(cudaFree(m->adam_cnt));
+    m->adam_cnt = nullptr;
+    m->adam_cnt_n = 0;
+    CK(cudaMalloc(&m->adam_cnt, sizeof(int) * (size_t)max_inst));
+    CK(cudaMemset(m->adam_cnt, 0, sizeof(int) * (size_t)max_inst));
+    m->adam_cnt_n = max_inst;
+  }
   return ensure_ws(m, need, nullptr);
+}
+
+lrnr_status lrnr_set_tuning(lrnr_model *m, lrnr_form form, lrnr_precision prec, int nt,
+                            int ctas_per_sm) {
+  if (!m || (form != LRNR_FULL && form != LRNR_FAST) || prec < LRNR_FP32 || prec > LRNR_BF16X3)
+    return LRNR_EINVAL;
+  if (nt != 0 && nt != 32 && nt != 64 && nt != 128) return LRNR_EINVAL;
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return LRNR_EINVAL;
+  m->tune_nt[form][prec] = nt;
+  m->tune_cta[form][prec] = ctas_per_sm;
+  return LRNR_OK;
 }
 
 lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int *sum_m,
@@ -744,6 +811,7 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->rows_dev);
   cudaFree(m->status_dev);
   cudaFree(m->ws);
+  cudaFree(m->adam_cnt);
   for (auto e : m->ev_start) cudaEventDestroy(e);
   for (auto e : m->ev_stop) cudaEventDestroy(e);
   for (auto e : m->cap_start) cudaEventDestroy(e);

@@ -16,16 +16,21 @@
 namespace lrnr {
 namespace {
 
+// Shared memory (floats): the tile's s and one partial row per warp.  The rank-r
+// layer inputs are kept in a per-CTA global scratch area ([slot][thread], L2-resident).
 template <int RM, int NT>
 struct FullLayout {
-  int s, q, red, total;
+  int s, red, total;
   __host__ __device__ FullLayout(int L, int P) {
     s = 0;
-    q = s + (L + 1) * RM;
-    red = q + (L > 1 ? (L - 1) : 0) * 4 * RM * NT;
+    red = s + (L + 1) * RM;
     total = red + (NT / 32) * P;
   }
 };
+
+__host__ __device__ inline size_t full_store_floats(int L, int RM, int NT) {
+  return (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * NT;
+}
 
 template <int RM, int NI>
 __device__ __forceinline__ void load_row(const float *__restrict__ W, float (&w)[RM]) {
@@ -240,7 +245,7 @@ __global__ void __launch_bounds__(NT) k_full_fp32(const __grid_constant__ KParam
   const int L = p.L;
   const FullLayout<RM, NT> lay(L, p.P);
   float *s_s = smem + lay.s;
-  float *q_s = smem + lay.q;
+  float *q_s = p.scratch + (size_t)blockIdx.x * full_store_floats(L, RM, NT);
   float *red_s = smem + lay.red;
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
   const int ntiles = __ldg(p.tile_off + p.n_inst);
@@ -273,26 +278,38 @@ __global__ void __launch_bounds__(NT) k_full_fp32(const __grid_constant__ KParam
 }
 
 template <int RM, int NT>
-cudaError_t launch_full_t(const KParams &p, int grid_cap, cudaStream_t st) {
+cudaError_t launch_full_t(const KParams &p, int grid, cudaStream_t st) {
   const FullLayout<RM, NT> lay(p.L, p.P);
   const size_t bytes = (size_t)lay.total * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_full_fp32<RM, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  int per_sm = 0, dev = 0, sms = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_full_fp32<RM, NT>, NT, bytes);
-  if (e != cudaSuccess) return e;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(grid_cap, std::max(1, per_sm) * sms));
-  k_full_fp32<RM, NT><<<grid, NT, bytes, st>>>(p);
+  k_full_fp32<RM, NT><<<std::max(1, grid), NT, bytes, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int RM, int NT>
+int ctas_per_sm_t(const KParams &p) {
+  const FullLayout<RM, NT> lay(p.L, p.P);
+  const size_t bytes = (size_t)lay.total * sizeof(float);
+  if (cudaFuncSetAttribute(k_full_fp32<RM, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes) != cudaSuccess)
+    return 1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_full_fp32<RM, NT>, NT, bytes) !=
+      cudaSuccess)
+    return 1;
+  return std::max(1, per_sm);
 }
 
 }  // namespace
 
 size_t full_fp32_smem_bytes(int L, int RM, int NT, int P) {
-  return (size_t)((L + 1) * RM + (L > 1 ? L - 1 : 0) * 4 * RM * NT + (NT / 32) * P) * sizeof(float);
+  return (size_t)((L + 1) * RM + (NT / 32) * P) * sizeof(float);
+}
+
+size_t full_fp32_scratch_floats(int L, int RM, int NT, int grid) {
+  return full_store_floats(L, RM, NT) * (size_t)grid;
 }
 
 int full_fp32_choose_nt(int L, int RM, int P) {
@@ -302,15 +319,29 @@ int full_fp32_choose_nt(int L, int RM, int P) {
   return 0;
 }
 
-cudaError_t launch_full_fp32(const KParams &p, int grid_cap, cudaStream_t st) {
+int full_fp32_ctas_per_sm(const KParams &p) {
   if (p.nt == 64) {
-    if (p.RM == 8) return launch_full_t<8, 64>(p, grid_cap, st);
-    if (p.RM == 16) return launch_full_t<16, 64>(p, grid_cap, st);
-    if (p.RM == 32) return launch_full_t<32, 64>(p, grid_cap, st);
+    if (p.RM == 8) return ctas_per_sm_t<8, 64>(p);
+    if (p.RM == 16) return ctas_per_sm_t<16, 64>(p);
+    if (p.RM == 32) return ctas_per_sm_t<32, 64>(p);
   } else if (p.nt == 32) {
-    if (p.RM == 8) return launch_full_t<8, 32>(p, grid_cap, st);
-    if (p.RM == 16) return launch_full_t<16, 32>(p, grid_cap, st);
-    if (p.RM == 32) return launch_full_t<32, 32>(p, grid_cap, st);
+    if (p.RM == 8) return ctas_per_sm_t<8, 32>(p);
+    if (p.RM == 16) return ctas_per_sm_t<16, 32>(p);
+    if (p.RM == 32) return ctas_per_sm_t<32, 32>(p);
+  }
+  return 1;
+}
+
+cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st) {
+  if (!p.scratch && p.grad) return cudaErrorInvalidValue;
+  if (p.nt == 64) {
+    if (p.RM == 8) return launch_full_t<8, 64>(p, grid, st);
+    if (p.RM == 16) return launch_full_t<16, 64>(p, grid, st);
+    if (p.RM == 32) return launch_full_t<32, 64>(p, grid, st);
+  } else if (p.nt == 32) {
+    if (p.RM == 8) return launch_full_t<8, 32>(p, grid, st);
+    if (p.RM == 16) return launch_full_t<16, 32>(p, grid, st);
+    if (p.RM == 32) return launch_full_t<32, 32>(p, grid, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -53,7 +53,9 @@ struct KParams {
   float *u, *ut, *ux, *uxx, *res, *res_ic, *res_bc;
   int64_t *step;               // spinprop: incremented once by block 0
   int *status;
-  float *scratch;              // tensor-core path: per-CTA store of layer inputs
+  float *scratch;              // per-CTA store of layer inputs (FP32 and tensor-core kernels)
+  int fused_tiles;             // the tile kernel computes the tile offsets itself
+  int fast_regs;               // FastLRNR kernel build: 3 = 168 registers, else 255
   uint32_t max_wait;           // iteration cap of every device-side wait
 };
 
@@ -91,16 +93,56 @@ struct Tile {
   int count;       // points (or pairs) in this tile
 };
 
-__device__ __forceinline__ Tile decode_tile(const KParams &p, int tile) {
+// Tiles of instance i: interior and initial points nt per tile, periodic pairs
+// nt/2 per tile.
+__device__ __forceinline__ int32_t tiles_of(const int64_t *io, const int64_t *co, const int64_t *bo,
+                                            int i, int nt) {
+  const int64_t nI = io[i + 1] - io[i], nC = co[i + 1] - co[i], nB = bo[i + 1] - bo[i];
+  const int half = nt / 2;
+  return (int32_t)((nI + nt - 1) / nt + (nC + nt - 1) / nt + (nB + half - 1) / half);
+}
+
+// Tile offsets computed by one CTA into shared memory (toff_s[n_inst + 1]); used by
+// kernels that fuse the tile schedule.  Block 0 also publishes them to p.tile_off
+// for the reduction kernel that runs next.  Call with all threads of the block.
+__device__ __forceinline__ void block_tile_offsets(const KParams &p, int32_t *toff_s,
+                                                   int32_t *scan_s) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int chunk = (p.n_inst + nth - 1) / nth;
+  const int b = tid * chunk, e = min(p.n_inst, b + chunk);
+  int32_t acc = 0;
+  for (int i = b; i < e; ++i) acc += tiles_of(p.int_off, p.ic_off, p.bc_off, i, p.nt);
+  scan_s[tid] = acc;
+  __syncthreads();
+  for (int off = 1; off < nth; off *= 2) {
+    const int32_t v = tid >= off ? scan_s[tid - off] : 0;
+    __syncthreads();
+    scan_s[tid] += v;
+    __syncthreads();
+  }
+  int32_t run = scan_s[tid] - acc;
+  for (int i = b; i < e; ++i) {
+    toff_s[i] = run;
+    run += tiles_of(p.int_off, p.ic_off, p.bc_off, i, p.nt);
+  }
+  if (tid == nth - 1) toff_s[p.n_inst] = scan_s[nth - 1];
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int i = tid; i <= p.n_inst; i += nth) const_cast<int32_t *>(p.tile_off)[i] = toff_s[i];
+}
+
+__device__ __forceinline__ Tile decode_tile(const KParams &p, int tile,
+                                            const int32_t *toff = nullptr) {
+  if (!toff) toff = p.tile_off;
   // largest i with tile_off[i] <= tile
   int lo = 0, hi = p.n_inst - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (__ldg(p.tile_off + mid) <= tile) lo = mid; else hi = mid - 1;
+    if (toff[mid] <= tile) lo = mid; else hi = mid - 1;
   }
   Tile t;
   t.inst = lo;
-  int j = tile - __ldg(p.tile_off + lo);
+  int j = tile - toff[lo];
   int64_t a = __ldg(p.int_off + lo), nI = __ldg(p.int_off + lo + 1) - a;
   int ntI = (int)((nI + p.nt - 1) / p.nt);
   if (j < ntI) {
@@ -167,19 +209,25 @@ int fast_ctas_per_sm(const KParams &p);                 // resident CTAs of k_fa
 size_t fast_scratch_floats(int L, int RM, int NT, int grid);  // layer-input store
 size_t full_fp32_smem_bytes(int L, int RM, int NT, int P);
 int full_fp32_choose_nt(int L, int RM, int P);
+int full_fp32_ctas_per_sm(const KParams &p);
+size_t full_fp32_scratch_floats(int L, int RM, int NT, int grid);
 cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_t st);
 // grid_cap bounds the persistent grid (never more CTAs than tiles); the FastLRNR
 // kernel is launched with exactly `grid` CTAs (its scratch is sized for them).
 cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
-cudaError_t launch_full_fp32(const KParams &p, int grid_cap, cudaStream_t st);
+cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int grid_cap,
                            cudaStream_t st);
 cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,
                           int rows_stride, float *loss_out, float *dL_ds, float *dL_db,
                           int sum_m, cudaStream_t st);
+// gsum (n_inst x groups x entries floats) and cnt (n_inst zeroed ints) select the
+// two-level reduction; with nullptr the one-block-per-instance kernel runs.
 cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
                                float lr, float b1, float b2, float eps, float lam,
-                               const float *anchor, float *loss_out, cudaStream_t st);
+                               const float *anchor, float *loss_out, float *gsum, int *cnt,
+                               cudaStream_t st);
+size_t adam_group_floats(int n_inst, int L, int RM);
 cudaError_t launch_eim_greedy(double *R, int M, int64_t K, int rhat, double tol, int32_t *rows,
                               double *Xi, int *used_dev, double *colmax, int64_t *colarg,
                               int *status, cudaStream_t st);

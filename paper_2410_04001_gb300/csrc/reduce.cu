@@ -5,13 +5,6 @@
 namespace lrnr {
 namespace {
 
-__device__ __forceinline__ int32_t tiles_of(const int64_t *io, const int64_t *co, const int64_t *bo,
-                                            int i, int nt) {
-  const int64_t nI = io[i + 1] - io[i], nC = co[i + 1] - co[i], nB = bo[i + 1] - bo[i];
-  const int half = nt / 2;
-  return (int32_t)((nI + nt - 1) / nt + (nC + nt - 1) / nt + (nB + half - 1) / half);
-}
-
 // tile_off[i] = first tile of instance i (exclusive prefix sum); one block.
 __global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *io, const int64_t *co,
                                                        const int64_t *bo, int n_inst, int nt,
@@ -180,6 +173,80 @@ __global__ void __launch_bounds__(1024) k_reduce_adam(const __grid_constant__ Ad
   }
 }
 
+// Two-level version for the SPInProp step: block (i, g) sums the partial rows
+// t = t0 + g, t0 + g + TG, ... of instance i for every entry and writes one group
+// row; the last block of instance i to finish (atomic ticket) adds the TG group
+// rows in order and applies Adam.  Deterministic: the order of every sum is fixed.
+constexpr int kAdamGroups = 32;
+
+__global__ void __launch_bounds__(256) k_reduce_adam2(const __grid_constant__ AdamArgs A,
+                                                      float *__restrict__ gsum, int *cnt) {
+  const RedArgs &a = A.red;
+  __shared__ float gsh[(LMAX + 1) * RMAX];
+  __shared__ float lsum[8];
+  __shared__ float loss_sh;
+  __shared__ int last;
+  const int i = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
+  const int DB0 = 1 + (a.L + 1) * a.RM;
+  float *grow = gsum + ((int64_t)i * kAdamGroups + g) * DB0;
+  for (int j = tid; j < DB0; j += 256) {
+    float a0 = 0.0f, a1 = 0.0f;
+    int t = t0 + g;
+    for (; t + kAdamGroups < t1; t += 2 * kAdamGroups) {
+      a0 += __ldg(a.partial + (int64_t)t * a.P + j);
+      a1 += __ldg(a.partial + (int64_t)(t + kAdamGroups) * a.P + j);
+    }
+    if (t < t1) a0 += __ldg(a.partial + (int64_t)t * a.P + j);
+    grow[j] = a0 + a1;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&cnt[i], 1) == kAdamGroups - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const float *gi = gsum + (int64_t)i * kAdamGroups * DB0;
+  for (int j = tid; j < DB0; j += 256) {
+    float tot = 0.0f;
+    for (int gg = 0; gg < kAdamGroups; ++gg) tot += __ldcg(gi + gg * DB0 + j);
+    if (j == 0) loss_sh = tot;
+    else {
+      const int l = (j - 1) / a.RM, k = (j - 1) % a.RM;
+      if (k < a.r[l]) gsh[a.roff[l] + k] = tot;
+    }
+  }
+  __syncthreads();
+  const int64_t k = *A.step;
+  const float bc1 = 1.0f - powf(A.b1, (float)k);
+  const float bc2 = 1.0f - powf(A.b2, (float)k);
+  float loc = 0.0f;
+  for (int q = tid; q < a.sum_r; q += 256) {
+    const int64_t o = (int64_t)i * a.sum_r + q;
+    const float sv = A.s[o];
+    float gr = gsh[q];
+    if (A.anchor) {
+      const float d = sv - A.anchor[o];
+      loc += A.lam * fabsf(d);
+      gr += A.lam * (float)((d > 0.0f) - (d < 0.0f));
+    }
+    const float mv = A.b1 * A.m[o] + (1.0f - A.b1) * gr;
+    const float vv = A.b2 * A.v[o] + (1.0f - A.b2) * gr * gr;
+    A.m[o] = mv;
+    A.v[o] = vv;
+    A.s[o] = sv - A.lr * (mv / bc1) / (sqrtf(vv / bc2) + A.eps);
+  }
+  loc = warp_sum(loc);
+  if ((tid & 31) == 0) lsum[tid >> 5] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    float lt = 0.0f;
+    for (int w = 0; w < 8; ++w) lt += lsum[w];
+    if (a.loss_out) a.loss_out[i] = loss_sh + lt;
+    cnt[i] = 0;   // ready for the next step
+  }
+}
+
 void fill_red(RedArgs &a, const KParams &p, int n_needed, int fast, const int32_t *rows,
               float *loss_out, float *dL_ds, float *dL_db, int sum_m) {
   a.partial = p.partial;
@@ -221,7 +288,8 @@ cudaError_t launch_reduce(const KParams &p, int n_needed, int form_fast, const i
 
 cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
                                float lr, float b1, float b2, float eps, float lam,
-                               const float *anchor, float *loss_out, cudaStream_t st) {
+                               const float *anchor, float *loss_out, float *gsum, int *cnt,
+                               cudaStream_t st) {
   AdamArgs A;
   fill_red(A.red, p, 1 + (p.L + 1) * p.RM, 0, nullptr, loss_out, nullptr, nullptr, 0);
   A.s = s;
@@ -234,8 +302,16 @@ cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, c
   A.eps = eps;
   A.lam = lam;
   A.anchor = anchor;
-  k_reduce_adam<<<p.n_inst, dim3(32, 32), 0, st>>>(A);
+  if (gsum && cnt) {
+    k_reduce_adam2<<<dim3(p.n_inst, kAdamGroups), 256, 0, st>>>(A, gsum, cnt);
+  } else {
+    k_reduce_adam<<<p.n_inst, dim3(32, 32), 0, st>>>(A);
+  }
   return cudaGetLastError();
+}
+
+size_t adam_group_floats(int n_inst, int L, int RM) {
+  return (size_t)n_inst * kAdamGroups * partial_db0(L, RM);
 }
 
 }  // namespace lrnr
