@@ -2,14 +2,14 @@
 //
 // One thread per collocation point.  The reduced bases (Uhat, bhat, Vhat: a few KB
 // per layer) and the tile's coefficients s live in shared memory and are read
-// with warp-uniform (broadcast) loads.  Each layer streams over its rhat rows: for
-// row i the thread forms the pre-activation jet a_i = Uhat_i . (s * zhat) (+ bhat_i)
-// (four scalars, one per jet channel), pushes it through tanh and accumulates the
-// next rank-r jet zhat' += Vhat_i w_i; the reverse sweep does the same per row for
-// the adjoint.  Rank-r vectors are held as pairs of adjacent entries so that the
+// with warp-uniform (broadcast) loads.  Each layer streams over its rhat rows in
+// blocks of four: for row i the thread forms the pre-activation jet
+// a_i = Uhat_i . (s * zhat) (+ bhat_i) (four scalars, one per jet channel), pushes it
+// through tanh and accumulates the next rank-r jet zhat' += Vhat_i w_i; the reverse
+// sweep does the same per row for the adjoint.  Rank-r vectors are held as pairs of adjacent entries so that the
 // products run on the packed two-lane FP32 FMA (two multiply-adds per instruction;
-// each lane rounds exactly like a scalar fmaf).  Row loops are not unrolled, which
-// keeps the kernel small enough for the instruction cache.  The forward keeps each
+// each lane rounds exactly like a scalar fmaf).  Only the four rows of a block are
+// unrolled, which keeps the kernel small enough for the instruction cache.  The forward keeps each
 // hidden layer's input jet in a per-CTA global scratch area ([slot][thread],
 // coalesced, L2-resident) so the reverse sweep can rebuild pre-activations without
 // re-running the network.  Per-layer gradient pieces are summed over the warp and
@@ -24,16 +24,21 @@
 
 namespace lrnr {
 
-// Shared memory of one CTA (floats): the reduced bases, the tile's s, the staged
-// pre-activation adjoints of the current layer [row][thread][channel], one partial
-// row per warp and, when the kernel computes the tile schedule, the tile offsets.
+// Shared memory of one CTA (floats): the reduced bases, the tile's s, the tile's
+// scaled input bases Uhat diag(s^l) per layer, the staged pre-activation adjoints
+// of the current layer [row][thread] (float4: the four channels), the staging
+// buffer of the next reverse layer's input jet [channel][quad][thread] (float4), one
+// partial row per warp and, when the kernel computes the tile schedule, the tile
+// offsets.
 struct FastLayout {
-  int pack, s, ab, red, toff, scan, total;
+  int pack, s, us, ab, qb, red, toff, scan, total;
   __host__ __device__ FastLayout(int L, int RM, int RH, int NT, int P, int fused_inst = 0) {
     pack = 0;
     s = (fast_pack_floats(L, RM, RH) + 3) & ~3;
-    ab = (s + (L + 1) * RM + 3) & ~3;
-    red = ab + 4 * RH * NT;
+    us = (s + (L + 1) * RM + 3) & ~3;
+    ab = us + L * RH * RM;
+    qb = ab + 4 * RH * NT;
+    red = qb + 4 * RM * NT;
     toff = red + (NT / 32) * P;
     scan = toff + (fused_inst ? fused_inst + 1 : 0);
     total = scan + (fused_inst ? NT : 0);
@@ -58,92 +63,155 @@ struct Jet {
   float2 v[C][RM / 2];
 };
 
-// The input jet of hidden layer l: stored by the forward (l > 0) or rebuilt from
-// the point (l == 0: zhat^0 = V^0^T z^0).
+// The input jet of the first hidden layer, zhat^0 = V^0^T z^0 with z^0 = (x, t)
+// and its derivative channels.
 template <int RM, int C>
-__device__ __forceinline__ void load_input(int l, const float2 *__restrict__ q_g, int NT, int tid,
-                                           const float *V0, float x, float t, Jet<C, RM> &q) {
-  if (l > 0) {
+__device__ __forceinline__ void input_jet(const float *V0, float x, float t, Jet<C, RM> &q) {
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+  for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int h = 0; h < RM / 2; ++h) q.v[c][h] = q_g[(((l - 1) * 4 + c) * (RM / 2) + h) * NT + tid];
-  } else {
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int h = 0; h < RM / 2; ++h) q.v[c][h] = make_float2(0.0f, 0.0f);
-    // R1 = 2: entries 0 and 1 form the first pair
-    q.v[0][0] = make_float2(V0[0] * x + V0[R1] * t, V0[1] * x + V0[R1 + 1] * t);
-    if constexpr (C >= 3) {
-      q.v[1][0] = make_float2(V0[R1], V0[R1 + 1]);
-      q.v[2][0] = make_float2(V0[0], V0[1]);
-    }
+    for (int h = 0; h < RM / 2; ++h) q.v[c][h] = make_float2(0.0f, 0.0f);
+  // R1 = 2: entries 0 and 1 form the first pair
+  q.v[0][0] = make_float2(V0[0] * x + V0[R1] * t, V0[1] * x + V0[R1 + 1] * t);
+  if constexpr (C >= 3) {
+    q.v[1][0] = make_float2(V0[R1], V0[R1 + 1]);
+    q.v[2][0] = make_float2(V0[0], V0[1]);
   }
 }
 
+// Layer-input store of the forward (hidden layer l > 0), per CTA in global memory:
+// [l-1][channel][quad][thread] float4, four rank entries per float4.
 template <int RM, int C>
-__device__ __forceinline__ void store_input(int l, float2 *__restrict__ q_g, int NT, int tid,
+__device__ __forceinline__ void store_input(int l, float4 *__restrict__ q_g, int NT, int tid,
                                             const Jet<C, RM> &q) {
 #pragma unroll
   for (int c = 0; c < C; ++c)
 #pragma unroll
-    for (int h = 0; h < RM / 2; ++h) q_g[(((l - 1) * 4 + c) * (RM / 2) + h) * NT + tid] = q.v[c][h];
+    for (int h = 0; h < RM / 4; ++h)
+      q_g[(((l - 1) * 4 + c) * (RM / 4) + h) * NT + tid] =
+          make_float4(q.v[c][2 * h].x, q.v[c][2 * h].y, q.v[c][2 * h + 1].x, q.v[c][2 * h + 1].y);
 }
 
-// out[c] += W[0..NI) . v[c][0..NI), accumulated as even/odd partial sums.
+// Start copying the thread's stored input jet of layer l into the staging buffer
+// (cp.async, L2 -> shared memory without registers); each thread copies and later
+// reads only its own entries.
+template <int RM, int C>
+__device__ __forceinline__ void prefetch_input(int l, const float4 *__restrict__ q_g, float4 *q_b,
+                                               int NT, int tid) {
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int h = 0; h < RM / 4; ++h) {
+      const float4 *src = q_g + (((l - 1) * 4 + c) * (RM / 4) + h) * NT + tid;
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(q_b + (c * (RM / 4) + h) * NT + tid);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Wait for the thread's copies and read the staged jet.
+template <int RM, int C>
+__device__ __forceinline__ void load_staged(const float4 *q_b, int NT, int tid, Jet<C, RM> &q) {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int h = 0; h < RM / 4; ++h) {
+      const float4 v = q_b[(c * (RM / 4) + h) * NT + tid];
+      q.v[c][2 * h] = make_float2(v.x, v.y);
+      q.v[c][2 * h + 1] = make_float2(v.z, v.w);
+    }
+}
+
+// Rows are processed in blocks of RB: one block's dot products are RB * C
+// independent accumulation chains and its tanh jets RB independent chains, which
+// the scheduler interleaves (at two warps per scheduler a single row's dependent
+// chain would leave the FMA pipe idle).  Rows past rhat are zero in the pack, so a
+// block may run past the last selected row: its pre-activation is zero and its
+// outgoing weights are zero.
+constexpr int RB = 4;
+
+// out[r][c] += W_r[0..NI) . v[c][0..NI) for the RB rows W_r = W + r * RM, each
+// accumulated as even/odd partial sums.
 template <int RM, int NI, int C>
-__device__ __forceinline__ void row_dot(const float *__restrict__ W, const Jet<C, RM> &v,
-                                        float (&out)[C]) {
-  float2 acc[C];
+__device__ __forceinline__ void block_dot(const float *__restrict__ W, const Jet<C, RM> &v,
+                                          float (&out)[RB][C]) {
+  if constexpr (NI == 1) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) acc[c] = make_float2(out[c], 0.0f);
-  if constexpr (NI % 4 == 0) {
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int k = 0; k < NI; k += 4) {
-      const float4 w = *reinterpret_cast<const float4 *>(W + k);
-      const float2 w01 = make_float2(w.x, w.y), w23 = make_float2(w.z, w.w);
+      for (int c = 0; c < C; ++c) out[r][c] = fmaf(W[r * RM], v.v[c][0].x, out[r][c]);
+  } else {
+    static_assert(NI == 2 || NI % 4 == 0, "input rank");
+    float2 acc[RB][C];
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        acc[c] = f2fma(w01, v.v[c][k / 2], acc[c]);
-        acc[c] = f2fma(w23, v.v[c][k / 2 + 1], acc[c]);
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[r][c] = make_float2(out[r][c], 0.0f);
+    if constexpr (NI == 2) {
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const float2 w = *reinterpret_cast<const float2 *>(W + r * RM);
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] = f2fma(w, v.v[c][0], acc[r][c]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NI; k += 4) {
+        float4 w[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) w[r] = *reinterpret_cast<const float4 *>(W + r * RM + k);
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+            acc[r][c] = f2fma(make_float2(w[r].x, w[r].y), v.v[c][k / 2], acc[r][c]);
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+            acc[r][c] = f2fma(make_float2(w[r].z, w[r].w), v.v[c][k / 2 + 1], acc[r][c]);
       }
     }
-  } else if constexpr (NI == 2) {
-    const float2 w01 = *reinterpret_cast<const float2 *>(W);
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = f2fma(w01, v.v[c][0], acc[c]);
-  } else {   // NI == 1
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c].x = fmaf(W[0], v.v[c][0].x, acc[c].x);
+      for (int c = 0; c < C; ++c) out[r][c] = acc[r][c].x + acc[r][c].y;
   }
-#pragma unroll
-  for (int c = 0; c < C; ++c) out[c] = acc[c].x + acc[c].y;
 }
 
-// acc[c][0..NI) += W[0..NI) * v[c]
-template <int RM, int NI, int C>
-__device__ __forceinline__ void row_axpy(const float *__restrict__ W, const float (&v)[C],
-                                         Jet<C, RM> &acc) {
-  if constexpr (NI % 4 == 0) {
+// acc[c][0..NO) += sum over the RB rows (in row order) of W_r[0..NO) * z[r][c].
+template <int RM, int NO, int C>
+__device__ __forceinline__ void block_axpy(const float *__restrict__ W, const float (&z)[RB][C],
+                                           Jet<C, RM> &acc) {
+  if constexpr (NO == 1) {
 #pragma unroll
-    for (int k = 0; k < NI; k += 4) {
-      const float4 w = *reinterpret_cast<const float4 *>(W + k);
-      const float2 w01 = make_float2(w.x, w.y), w23 = make_float2(w.z, w.w);
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const float2 vc = splat(v[c]);
-        acc.v[c][k / 2] = f2fma(w01, vc, acc.v[c][k / 2]);
-        acc.v[c][k / 2 + 1] = f2fma(w23, vc, acc.v[c][k / 2 + 1]);
-      }
+      for (int c = 0; c < C; ++c) acc.v[c][0].x = fmaf(W[r * RM], z[r][c], acc.v[c][0].x);
+  } else if constexpr (NO == 2) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const float2 w = *reinterpret_cast<const float2 *>(W + r * RM);
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc.v[c][0] = f2fma(w, splat(z[r][c]), acc.v[c][0]);
     }
-  } else if constexpr (NI == 2) {
-    const float2 w01 = *reinterpret_cast<const float2 *>(W);
+  } else {
+    static_assert(NO % 4 == 0, "output rank");
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc.v[c][0] = f2fma(w01, splat(v[c]), acc.v[c][0]);
-  } else {   // NI == 1
+    for (int k = 0; k < NO; k += 4) {
+      float4 w[RB];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc.v[c][0].x = fmaf(W[0], v[c], acc.v[c][0].x);
+      for (int r = 0; r < RB; ++r) w[r] = *reinterpret_cast<const float4 *>(W + r * RM + k);
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float2 zz = splat(z[r][c]);
+          acc.v[c][k / 2] = f2fma(make_float2(w[r].x, w[r].y), zz, acc.v[c][k / 2]);
+          acc.v[c][k / 2 + 1] = f2fma(make_float2(w[r].z, w[r].w), zz, acc.v[c][k / 2 + 1]);
+        }
+    }
   }
 }
 
@@ -204,21 +272,25 @@ __device__ __forceinline__ void layer_fwd(const float *__restrict__ Uh, const fl
                                           const float *__restrict__ Vh, int nrows,
                                           const Jet<C, RM> &y, Jet<C, RM> &qn) {
 #pragma unroll 1
-  for (int i = 0; i < nrows; ++i) {
-    float a[C];
-    a[0] = bh[i];
+  for (int i = 0; i < nrows; i += RB) {
+    float a[RB][C];
 #pragma unroll
-    for (int c = 1; c < C; ++c) a[c] = 0.0f;
-    row_dot<RM, NI, C>(Uh + i * RM, y, a);
-    jet_fwd<C>(a);
-    row_axpy<RM, NO, C>(Vh + i * RM, a, qn);
+    for (int r = 0; r < RB; ++r) {
+      a[r][0] = bh[i + r];
+#pragma unroll
+      for (int c = 1; c < C; ++c) a[r][c] = 0.0f;
+    }
+    block_dot<RM, NI, C>(Uh + i * RM, y, a);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) jet_fwd<C>(a[r]);
+    block_axpy<RM, NO, C>(Vh + i * RM, a, qn);
   }
 }
 
 // One reduced layer reverse, in two passes over the rows so that no more than two
 // rank-r jets are live at once:
 //   pass 1: rebuild a_i = Uhat_i . y (+ bhat_i), pull wb_i = Vhat_i . qb back through
-//           the tanh jet, stage abar_i (all channels) in ab_s[row][thread][channel];
+//           the tanh jet, stage abar_i (all channels) in ab_s[row][thread];
 //   pass 2: pb = Uhat^T abar from the staged rows.
 template <int RM, int C, int NI, int NO>
 __device__ __forceinline__ void layer_bwd(const float *__restrict__ Uh, const float *__restrict__ bh,
@@ -226,39 +298,48 @@ __device__ __forceinline__ void layer_bwd(const float *__restrict__ Uh, const fl
                                           const Jet<C, RM> &y, const Jet<C, RM> &qb,
                                           float4 *ab_s, int NT) {
 #pragma unroll 1
-  for (int i = 0; i < nrows; ++i) {
-    float a[C], wb[C];
-    a[0] = bh[i];
+  for (int i = 0; i < nrows; i += RB) {
+    float a[RB][C], wb[RB][C];
 #pragma unroll
-    for (int c = 1; c < C; ++c) a[c] = 0.0f;
+    for (int r = 0; r < RB; ++r) {
+      a[r][0] = bh[i + r];
 #pragma unroll
-    for (int c = 0; c < C; ++c) wb[c] = 0.0f;
-    row_dot<RM, NI, C>(Uh + i * RM, y, a);
-    row_dot<RM, NO, C>(Vh + i * RM, qb, wb);
-    jet_bwd<C>(a, wb);
-    float4 v = make_float4(wb[0], 0.0f, 0.0f, 0.0f);
-    if constexpr (C == 4) v = make_float4(wb[0], wb[1], wb[2], wb[3]);
-    ab_s[i * NT + threadIdx.x] = v;
+      for (int c = 1; c < C; ++c) a[r][c] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) wb[r][c] = 0.0f;
+    }
+    block_dot<RM, NI, C>(Uh + i * RM, y, a);
+    block_dot<RM, NO, C>(Vh + i * RM, qb, wb);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      jet_bwd<C>(a[r], wb[r]);
+      float4 v = make_float4(wb[r][0], 0.0f, 0.0f, 0.0f);
+      if constexpr (C == 4) v = make_float4(wb[r][0], wb[r][1], wb[r][2], wb[r][3]);
+      ab_s[(i + r) * NT + threadIdx.x] = v;
+    }
   }
 }
 
 template <int RM, int C, int NI>
 __device__ __forceinline__ void layer_bwd_pbar(const float *__restrict__ Uh, int nrows,
                                                const float4 *ab_s, int NT, Jet<C, RM> &pb) {
-#pragma unroll 2
-  for (int i = 0; i < nrows; ++i) {
-    const float4 v = ab_s[i * NT + threadIdx.x];
-    float ab[C];
-    ab[0] = v.x;
-    if constexpr (C == 4) { ab[1] = v.y; ab[2] = v.z; ab[3] = v.w; }
-    row_axpy<RM, NI, C>(Uh + i * RM, ab, pb);
+#pragma unroll 1
+  for (int i = 0; i < nrows; i += RB) {
+    float ab[RB][C];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const float4 v = ab_s[(i + r) * NT + threadIdx.x];
+      ab[r][0] = v.x;
+      if constexpr (C == 4) { ab[r][1] = v.y; ab[r][2] = v.z; ab[r][3] = v.w; }
+    }
+    block_axpy<RM, NI, C>(Uh + i * RM, ab, pb);
   }
 }
 
 template <int RM, int RH, int C>
 __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restrict__ w_s,
-                          const float *__restrict__ s_s, float2 *__restrict__ q_g, float4 *ab_s,
-                          float *red_w) {
+                          const float *__restrict__ us_s, const float *__restrict__ s_s,
+                          float4 *__restrict__ q_g, float4 *q_b, float4 *ab_s, float *red_w) {
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
   const int L = p.L;
@@ -270,22 +351,23 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
   const PointIn pt = load_point(p, T, tid);
   const float x = pt.x, t = pt.t;
 
-  // ---- forward: zhat^0 = V^0^T z^0, then the reduced layers (Eq. 2.8)
+  // ---- forward: zhat^0 = V^0^T z^0, then the reduced layers (Eq. 2.8) with the
+  // tile's scaled bases Uhat diag(s^l)
   Jet<C, RM> q;
-  load_input<RM, C>(0, q_g, NT, tid, V0, x, t, q);
+  input_jet<RM, C>(V0, x, t, q);
   for (int l = 0; l < L; ++l) {
-    const float *Uh = w_s + l * LS;
-    const float *bh = Uh + RH * RM;
+    const float *Us = us_s + l * RH * RM;
+    const float *bh = w_s + l * LS + RH * RM;
     const float *Vh = bh + RH;
     if (p.grad && l > 0) store_input<RM, C>(l, q_g, NT, tid, q);
-    Jet<C, RM> y = q;
-    jet_scale<RM, C>(y, s_s + l * RM);
-    jet_zero<RM, C>(q);
+    Jet<C, RM> qn;
+    jet_zero<RM, C>(qn);
     const int nr = p.rh[l];
-    if (l == 0 && l == L - 1) layer_fwd<RM, C, R1, 1>(Uh, bh, Vh, nr, y, q);
-    else if (l == 0) layer_fwd<RM, C, R1, RM>(Uh, bh, Vh, nr, y, q);
-    else if (l == L - 1) layer_fwd<RM, C, RM, 1>(Uh, bh, Vh, nr, y, q);
-    else layer_fwd<RM, C, RM, RM>(Uh, bh, Vh, nr, y, q);
+    if (l == 0 && l == L - 1) layer_fwd<RM, C, R1, 1>(Us, bh, Vh, nr, q, qn);
+    else if (l == 0) layer_fwd<RM, C, R1, RM>(Us, bh, Vh, nr, q, qn);
+    else if (l == L - 1) layer_fwd<RM, C, RM, 1>(Us, bh, Vh, nr, q, qn);
+    else layer_fwd<RM, C, RM, RM>(Us, bh, Vh, nr, q, qn);
+    q = qn;
   }
   const float sL = s_s[L * RM];
   float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -296,6 +378,7 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
   // ---- residual, loss and seeds (Eq. 4.1, Eq. 3.5 / 3.6)
   float ub[4], lp;
   if (!residual_and_seeds(p, T, pt, tid, u, ub, lp)) return;
+  if (L > 1) prefetch_input<RM, C>(L - 1, q_g, q_b, NT, tid);
 
   // ---- reverse sweep (backpropagation through the FastLRNR, Sec. 2.3)
   const int DB0 = partial_db0(L, RM);
@@ -320,43 +403,34 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
   }
   for (int l = L - 1; l >= 0; --l) {
     const float *Uh = w_s + l * LS;
+    const float *Us = us_s + l * RH * RM;
     const float *bh = Uh + RH * RM;
     const float *Vh = bh + RH;
     const float *sl = s_s + l * RM;
     const int nr = p.rh[l];
-    {
-      Jet<C, RM> y;
-      load_input<RM, C>(l, q_g, NT, tid, V0, x, t, y);
-      jet_scale<RM, C>(y, sl);
-      if (l == 0 && l == L - 1) layer_bwd<RM, C, R1, 1>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
-      else if (l == 0) layer_bwd<RM, C, R1, RM>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
-      else if (l == L - 1) layer_bwd<RM, C, RM, 1>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
-      else layer_bwd<RM, C, RM, RM>(Uh, bh, Vh, nr, y, qb, ab_s, NT);
+    // the layer's input jet (unscaled), live through both passes
+    Jet<C, RM> y;
+    if (l > 0) {
+      load_staged<RM, C>(q_b, NT, tid, y);
+      if (l > 1) prefetch_input<RM, C>(l - 1, q_g, q_b, NT, tid);
+    } else {
+      input_jet<RM, C>(V0, x, t, y);
     }
+    if (l == 0 && l == L - 1) layer_bwd<RM, C, R1, 1>(Us, bh, Vh, nr, y, qb, ab_s, NT);
+    else if (l == 0) layer_bwd<RM, C, R1, RM>(Us, bh, Vh, nr, y, qb, ab_s, NT);
+    else if (l == L - 1) layer_bwd<RM, C, RM, 1>(Us, bh, Vh, nr, y, qb, ab_s, NT);
+    else layer_bwd<RM, C, RM, RM>(Us, bh, Vh, nr, y, qb, ab_s, NT);
     Jet<C, RM> pb;
     jet_zero<RM, C>(pb);
     if (l == 0) layer_bwd_pbar<RM, C, R1>(Uh, nr, ab_s, NT, pb);
     else layer_bwd_pbar<RM, C, RM>(Uh, nr, ab_s, NT, pb);
-    // dL/ds^l = sum_c pbar_c * zhat_c (input jet, reloaded) and dL/dbhat^l rows
+    // dL/ds^l = sum_c pbar_c * zhat_c and the dL/dbhat^l rows
     float g[RM + RH];
 #pragma unroll
     for (int h = 0; h < RM / 2; ++h) {
       float2 d = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        float2 qv;
-        if (l > 0) {
-          qv = q_g[(((l - 1) * 4 + c) * (RM / 2) + h) * NT + tid];
-        } else {
-          qv = make_float2(0.0f, 0.0f);
-          if (h == 0) {
-            if (c == 0) qv = make_float2(V0[0] * x + V0[R1] * t, V0[1] * x + V0[R1 + 1] * t);
-            else if (c == 1) qv = make_float2(V0[R1], V0[R1 + 1]);
-            else if (c == 2) qv = make_float2(V0[0], V0[1]);
-          }
-        }
-        d = f2fma(pb.v[c][h], qv, d);
-      }
+      for (int c = 0; c < C; ++c) d = f2fma(pb.v[c][h], y.v[c][h], d);
       g[2 * h] = d.x;
       g[2 * h + 1] = d.y;
     }
@@ -376,6 +450,7 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
 // registers per thread; 2: up to 255 registers, no spills).
 template <int RM, int RH, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KParams p) {
+  static_assert(RH % RB == 0, "row blocks");
   extern __shared__ __align__(16) float smem[];
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
@@ -383,9 +458,11 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
   const FastLayout lay(L, RM, RH, NT, p.P, p.fused_tiles ? p.n_inst : 0);
   float *w_s = smem + lay.pack;
   float *s_s = smem + lay.s;
+  float *us_s = smem + lay.us;
   float4 *ab_s = reinterpret_cast<float4 *>(smem + lay.ab);
+  float4 *q_b = reinterpret_cast<float4 *>(smem + lay.qb);
   float *red_s = smem + lay.red;
-  float2 *q_g = reinterpret_cast<float2 *>(p.scratch + (size_t)blockIdx.x * fast_store_floats(L, RM, NT));
+  float4 *q_g = reinterpret_cast<float4 *>(p.scratch + (size_t)blockIdx.x * fast_store_floats(L, RM, NT));
   const int npack = fast_pack_floats(L, RM, RH);
   for (int i = tid; i < npack; i += NT) w_s[i] = __ldg(p.pack + i);
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
@@ -406,11 +483,19 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
     if (p.grad)
       for (int j = tid; j < (NT / 32) * p.P; j += NT) red_s[j] = 0.0f;
     __syncthreads();
+    {
+      const int LS = fast_layer_floats(RM, RH);
+      for (int j = tid; j < L * RH * RM; j += NT) {
+        const int l = j / (RH * RM), ik = j % (RH * RM);
+        us_s[j] = w_s[l * LS + ik] * s_s[l * RM + ik % RM];
+      }
+    }
+    __syncthreads();
     float *red_w = red_s + (tid >> 5) * p.P;
     if (T.kind == KIND_INT)
-      fast_tile<RM, RH, 4>(p, T, w_s, s_s, q_g, ab_s, red_w);
+      fast_tile<RM, RH, 4>(p, T, w_s, us_s, s_s, q_g, q_b, ab_s, red_w);
     else
-      fast_tile<RM, RH, 1>(p, T, w_s, s_s, q_g, ab_s, red_w);
+      fast_tile<RM, RH, 1>(p, T, w_s, us_s, s_s, q_g, q_b, ab_s, red_w);
     if (p.grad) {
       __syncthreads();
       for (int j = tid; j < p.P; j += NT) {
