@@ -269,7 +269,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     int per_sm = fast_ctas_per_sm(p);
     if (m->tune_cta[LRNR_FAST][prec] > 0) per_sm = std::min(per_sm, m->tune_cta[LRNR_FAST][prec]);
     ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
-    if (grad) scr_bytes = fast_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap) * sizeof(float);
+    if (grad) scr_bytes = fast_scratch_floats(m->L, p.RM, p.RH, p.nt, ps.grid_cap) * sizeof(float);
   } else {
     // the FP32 full-width kernel also keeps layer inputs in a per-CTA scratch
     int per_sm = full_fp32_ctas_per_sm(p);
@@ -706,7 +706,7 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   Pmax = std::max(Pmax, partial_len(m->L, RMAX, m->L * RHMAX + 1));
   // per-CTA layer-input stores (tensor-core and FastLRNR kernels): at most 4 CTAs per SM
   const size_t store = std::max(std::max(full_tc_scratch_floats(m->L, RMAX, m->num_sms),
-                                         fast_scratch_floats(m->L, RMAX, 128, 4 * m->num_sms)),
+                                         fast_scratch_floats(m->L, RMAX, RHMAX, 128, 4 * m->num_sms)),
                                 full_fp32_scratch_floats(m->L, RMAX, 64, 8 * m->num_sms));
   const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) +
                       align256((size_t)tiles * Pmax * sizeof(float)) +

@@ -20,8 +20,8 @@ int fast_choose_nt(int L, int RM, int RH, int P) {
   return 0;
 }
 
-size_t fast_scratch_floats(int L, int RM, int NT, int grid) {
-  return fast_store_floats(L, RM, NT) * (size_t)grid;
+size_t fast_scratch_floats(int L, int RM, int RH, int NT, int grid) {
+  return fast_store_floats(L, RM, RH, NT) * (size_t)grid;
 }
 
 int fast_ctas_per_sm(const KParams &p) {

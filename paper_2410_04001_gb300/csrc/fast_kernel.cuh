@@ -48,9 +48,14 @@ struct FastLayout {
 // Largest instance count for which the FastLRNR kernel computes its own tile offsets.
 constexpr int kFastFusedInstMax = 4096;
 
-// Floats of layer-input store per CTA (global scratch).
-__host__ __device__ inline size_t fast_store_floats(int L, int RM, int NT) {
+// Floats of the per-CTA global scratch of the gradient sweep: the layer-input store
+// ((L-1) layers x 4 channels x RM x NT) followed by the activation store (L layers x
+// RH rows x NT float4: tanh value and the three pre-activation derivative channels).
+__host__ __device__ inline size_t fast_input_store_floats(int L, int RM, int NT) {
   return (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * NT;
+}
+__host__ __device__ inline size_t fast_store_floats(int L, int RM, int RH, int NT) {
+  return fast_input_store_floats(L, RM, NT) + (size_t)L * RH * 4 * NT;
 }
 
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -233,11 +238,14 @@ __device__ __forceinline__ void jet_zero(Jet<C, RM> &q) {
     for (int h = 0; h < RM / 2; ++h) q.v[c][h] = make_float2(0.0f, 0.0f);
 }
 
-// tanh jet of one row, in place: a = (a0, a_t, a_x, a_xx) -> (z, z_t, z_x, z_xx).
+// tanh jet of one row, in place: a = (a0, a_t, a_x, a_xx) -> (z, z_t, z_x, z_xx); `keep`
+// receives what the adjoint needs: (z, a_t, a_x, a_xx).
 template <int C>
-__device__ __forceinline__ void jet_fwd(float (&a)[C]) {
+__device__ __forceinline__ void jet_fwd(float (&a)[C], float4 &keep) {
   float z, d1, d2;
   tanh_d(a[0], z, d1, d2);
+  keep = make_float4(z, 0.0f, 0.0f, 0.0f);
+  if constexpr (C == 4) keep = make_float4(z, a[1], a[2], a[3]);
   if constexpr (C == 4) a[3] = d2 * a[2] * a[2] + d1 * a[3];
   if constexpr (C >= 3) {
     a[1] *= d1;
@@ -246,31 +254,34 @@ __device__ __forceinline__ void jet_fwd(float (&a)[C]) {
   a[0] = z;
 }
 
-// Adjoint of jet_fwd: given the pre-activation a and the output adjoint wb,
-// overwrite wb with the pre-activation adjoint.
+// Adjoint of jet_fwd from its kept values k = (z, a_t, a_x, a_xx) and the output
+// adjoint wb: overwrite wb with the pre-activation adjoint.
 template <int C>
-__device__ __forceinline__ void jet_bwd(const float (&a)[C], float (&wb)[C]) {
-  float z, d1, d2;
-  tanh_d(a[0], z, d1, d2);
+__device__ __forceinline__ void jet_bwd(const float4 &k, float (&wb)[C]) {
+  static_assert(C == 1 || C == 4, "jet channels");
+  const float z = k.x;
+  const float d1 = 1.0f - z * z;
   float ab0 = wb[0] * d1;
-  if constexpr (C >= 3) ab0 += d2 * (wb[1] * a[1] + wb[2] * a[2]);
   if constexpr (C == 4) {
+    const float d2 = -2.0f * z * d1;
     const float d3 = d1 * (6.0f * z * z - 2.0f);
-    ab0 += wb[3] * (d3 * a[2] * a[2] + d2 * a[3]);
-    wb[2] = wb[2] * d1 + 2.0f * wb[3] * d2 * a[2];
+    ab0 += d2 * (wb[1] * k.y + wb[2] * k.z);
+    ab0 += wb[3] * (d3 * k.z * k.z + d2 * k.w);
+    wb[2] = wb[2] * d1 + 2.0f * wb[3] * d2 * k.z;
     wb[3] = wb[3] * d1;
-  } else if constexpr (C >= 3) {
-    wb[2] = wb[2] * d1;
+    wb[1] = wb[1] * d1;
   }
-  if constexpr (C >= 3) wb[1] = wb[1] * d1;
   wb[0] = ab0;
 }
 
-// One reduced layer forward: y (= s * zhat, input jet) -> qn (next rank-r jet).
+// One reduced layer forward: q (input jet; the bases are pre-scaled by s) -> qn
+// (next rank-r jet).  With a_g, each row's kept values go to the activation store
+// a_g[row][thread].
 template <int RM, int C, int NI, int NO>
-__device__ __forceinline__ void layer_fwd(const float *__restrict__ Uh, const float *__restrict__ bh,
+__device__ __forceinline__ void layer_fwd(const float *__restrict__ Us, const float *__restrict__ bh,
                                           const float *__restrict__ Vh, int nrows,
-                                          const Jet<C, RM> &y, Jet<C, RM> &qn) {
+                                          const Jet<C, RM> &y, Jet<C, RM> &qn,
+                                          float4 *__restrict__ a_g, int NT) {
 #pragma unroll 1
   for (int i = 0; i < nrows; i += RB) {
     float a[RB][C];
@@ -280,39 +291,41 @@ __device__ __forceinline__ void layer_fwd(const float *__restrict__ Uh, const fl
 #pragma unroll
       for (int c = 1; c < C; ++c) a[r][c] = 0.0f;
     }
-    block_dot<RM, NI, C>(Uh + i * RM, y, a);
+    block_dot<RM, NI, C>(Us + i * RM, y, a);
 #pragma unroll
-    for (int r = 0; r < RB; ++r) jet_fwd<C>(a[r]);
+    for (int r = 0; r < RB; ++r) {
+      float4 keep;
+      jet_fwd<C>(a[r], keep);
+      if (a_g) a_g[(i + r) * NT + threadIdx.x] = keep;
+    }
     block_axpy<RM, NO, C>(Vh + i * RM, a, qn);
   }
 }
 
 // One reduced layer reverse, in two passes over the rows so that no more than two
 // rank-r jets are live at once:
-//   pass 1: rebuild a_i = Uhat_i . y (+ bhat_i), pull wb_i = Vhat_i . qb back through
-//           the tanh jet, stage abar_i (all channels) in ab_s[row][thread];
+//   pass 1: pull wb_i = Vhat_i . qb back through the tanh jet using the values the
+//           forward kept (read one block ahead), stage abar_i (all channels) in
+//           ab_s[row][thread];
 //   pass 2: pb = Uhat^T abar from the staged rows.
-template <int RM, int C, int NI, int NO>
-__device__ __forceinline__ void layer_bwd(const float *__restrict__ Uh, const float *__restrict__ bh,
-                                          const float *__restrict__ Vh, int nrows,
-                                          const Jet<C, RM> &y, const Jet<C, RM> &qb,
+template <int RM, int C, int NO>
+__device__ __forceinline__ void layer_bwd(const float *__restrict__ Vh, int nrows,
+                                          const float4 *__restrict__ a_g, const Jet<C, RM> &qb,
                                           float4 *ab_s, int NT) {
 #pragma unroll 1
   for (int i = 0; i < nrows; i += RB) {
-    float a[RB][C], wb[RB][C];
+    float4 cur[RB];
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      a[r][0] = bh[i + r];
+    for (int r = 0; r < RB; ++r) cur[r] = a_g[(i + r) * NT + threadIdx.x];
+    float wb[RB][C];
 #pragma unroll
-      for (int c = 1; c < C; ++c) a[r][c] = 0.0f;
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int c = 0; c < C; ++c) wb[r][c] = 0.0f;
-    }
-    block_dot<RM, NI, C>(Uh + i * RM, y, a);
     block_dot<RM, NO, C>(Vh + i * RM, qb, wb);
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      jet_bwd<C>(a[r], wb[r]);
+      jet_bwd<C>(cur[r], wb[r]);
       float4 v = make_float4(wb[r][0], 0.0f, 0.0f, 0.0f);
       if constexpr (C == 4) v = make_float4(wb[r][0], wb[r][1], wb[r][2], wb[r][3]);
       ab_s[(i + r) * NT + threadIdx.x] = v;
@@ -339,7 +352,8 @@ __device__ __forceinline__ void layer_bwd_pbar(const float *__restrict__ Uh, int
 template <int RM, int RH, int C>
 __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restrict__ w_s,
                           const float *__restrict__ us_s, const float *__restrict__ s_s,
-                          float4 *__restrict__ q_g, float4 *q_b, float4 *ab_s, float *red_w) {
+                          float4 *__restrict__ q_g, float4 *__restrict__ a_g, float4 *q_b,
+                          float4 *ab_s, float *red_w) {
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
   const int L = p.L;
@@ -363,10 +377,11 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
     Jet<C, RM> qn;
     jet_zero<RM, C>(qn);
     const int nr = p.rh[l];
-    if (l == 0 && l == L - 1) layer_fwd<RM, C, R1, 1>(Us, bh, Vh, nr, q, qn);
-    else if (l == 0) layer_fwd<RM, C, R1, RM>(Us, bh, Vh, nr, q, qn);
-    else if (l == L - 1) layer_fwd<RM, C, RM, 1>(Us, bh, Vh, nr, q, qn);
-    else layer_fwd<RM, C, RM, RM>(Us, bh, Vh, nr, q, qn);
+    float4 *al = p.grad ? a_g + (size_t)l * RH * NT : nullptr;
+    if (l == 0 && l == L - 1) layer_fwd<RM, C, R1, 1>(Us, bh, Vh, nr, q, qn, al, NT);
+    else if (l == 0) layer_fwd<RM, C, R1, RM>(Us, bh, Vh, nr, q, qn, al, NT);
+    else if (l == L - 1) layer_fwd<RM, C, RM, 1>(Us, bh, Vh, nr, q, qn, al, NT);
+    else layer_fwd<RM, C, RM, RM>(Us, bh, Vh, nr, q, qn, al, NT);
     q = qn;
   }
   const float sL = s_s[L * RM];
@@ -403,9 +418,7 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
   }
   for (int l = L - 1; l >= 0; --l) {
     const float *Uh = w_s + l * LS;
-    const float *Us = us_s + l * RH * RM;
-    const float *bh = Uh + RH * RM;
-    const float *Vh = bh + RH;
+    const float *Vh = Uh + RH * RM + RH;
     const float *sl = s_s + l * RM;
     const int nr = p.rh[l];
     // the layer's input jet (unscaled), live through both passes
@@ -416,10 +429,9 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
     } else {
       input_jet<RM, C>(V0, x, t, y);
     }
-    if (l == 0 && l == L - 1) layer_bwd<RM, C, R1, 1>(Us, bh, Vh, nr, y, qb, ab_s, NT);
-    else if (l == 0) layer_bwd<RM, C, R1, RM>(Us, bh, Vh, nr, y, qb, ab_s, NT);
-    else if (l == L - 1) layer_bwd<RM, C, RM, 1>(Us, bh, Vh, nr, y, qb, ab_s, NT);
-    else layer_bwd<RM, C, RM, RM>(Us, bh, Vh, nr, y, qb, ab_s, NT);
+    const float4 *al = a_g + (size_t)l * RH * NT;
+    if (l == L - 1) layer_bwd<RM, C, 1>(Vh, nr, al, qb, ab_s, NT);
+    else layer_bwd<RM, C, RM>(Vh, nr, al, qb, ab_s, NT);
     Jet<C, RM> pb;
     jet_zero<RM, C>(pb);
     if (l == 0) layer_bwd_pbar<RM, C, R1>(Uh, nr, ab_s, NT, pb);
@@ -462,7 +474,9 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
   float4 *ab_s = reinterpret_cast<float4 *>(smem + lay.ab);
   float4 *q_b = reinterpret_cast<float4 *>(smem + lay.qb);
   float *red_s = smem + lay.red;
-  float4 *q_g = reinterpret_cast<float4 *>(p.scratch + (size_t)blockIdx.x * fast_store_floats(L, RM, NT));
+  float *store = p.scratch + (size_t)blockIdx.x * fast_store_floats(L, RM, RH, NT);
+  float4 *q_g = reinterpret_cast<float4 *>(store);
+  float4 *a_g = reinterpret_cast<float4 *>(store + fast_input_store_floats(L, RM, NT));
   const int npack = fast_pack_floats(L, RM, RH);
   for (int i = tid; i < npack; i += NT) w_s[i] = __ldg(p.pack + i);
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
@@ -493,9 +507,9 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
     __syncthreads();
     float *red_w = red_s + (tid >> 5) * p.P;
     if (T.kind == KIND_INT)
-      fast_tile<RM, RH, 4>(p, T, w_s, us_s, s_s, q_g, q_b, ab_s, red_w);
+      fast_tile<RM, RH, 4>(p, T, w_s, us_s, s_s, q_g, a_g, q_b, ab_s, red_w);
     else
-      fast_tile<RM, RH, 1>(p, T, w_s, us_s, s_s, q_g, q_b, ab_s, red_w);
+      fast_tile<RM, RH, 1>(p, T, w_s, us_s, s_s, q_g, a_g, q_b, ab_s, red_w);
     if (p.grad) {
       __syncthreads();
       for (int j = tid; j < p.P; j += NT) {

@@ -206,7 +206,7 @@ constexpr int kSmemBudget = 220 * 1024;   // dynamic shared memory a tile kernel
 size_t fast_smem_bytes(int L, int RM, int RH, int NT, int P);
 int fast_choose_nt(int L, int RM, int RH, int P);
 int fast_ctas_per_sm(const KParams &p);                 // resident CTAs of k_fast per SM
-size_t fast_scratch_floats(int L, int RM, int NT, int grid);  // layer-input store
+size_t fast_scratch_floats(int L, int RM, int RH, int NT, int grid);  // gradient-sweep store
 size_t full_fp32_smem_bytes(int L, int RM, int NT, int P);
 int full_fp32_choose_nt(int L, int RM, int P);
 int full_fp32_ctas_per_sm(const KParams &p);

@@ -71,7 +71,7 @@ extern "C" lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batc
       (size_t)tiles * (size_t)p.P * sizeof(float) > kScratchBytes - off_part)
     return LRNR_ETOOBIG;
   const size_t off_store = off_part + round256((size_t)tiles * (size_t)p.P * sizeof(float));
-  const size_t per_cta = fast_scratch_floats(p.L, p.RM, p.nt, 1) * sizeof(float);
+  const size_t per_cta = fast_scratch_floats(p.L, p.RM, p.RH, p.nt, 1) * sizeof(float);
   if (off_store > kScratchBytes || (kScratchBytes - off_store) / per_cta < 1) return LRNR_ETOOBIG;
   int sms = 1;
   int cur = -1;
