@@ -54,6 +54,11 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the FastLRNR kernel on this workload, from
+# one ncu capture of the current kernel (profiles/k_fast_cdr_single_m256_r16.md): the
+# mean of three launches of dram__bytes_read.sum + dram__bytes_write.sum.
+K_FAST_DRAM_BYTES = 49_869_568
+
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128
 
@@ -485,7 +490,7 @@ def main():
     peak = fp32_peak_tflops(sm_max)
     achieved = flops_launch / (k_avg_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": K_FAST_DRAM_BYTES,
             "kernel": "k_fast<16,16> (fused FastLRNR residual + adjoint)",
             "kernel_ms": k_avg_ms, "flops_per_launch": flops_launch,
             "peak_note": f"FP32 FMA peak = 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (max SM clock, {src} peaks file)"}

@@ -518,6 +518,8 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
         if (j == 0 && !isfinite(acc)) set_status(p.status, DEV_NONFINITE);
         p.partial[(int64_t)tile * p.P + j] = acc;
       }
+      // every read of the layer stores is behind the barrier above
+      l2_discard(store, fast_store_floats(L, RM, RH, NT) * sizeof(float));
     }
   }
 }

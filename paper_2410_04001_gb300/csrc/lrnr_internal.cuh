@@ -193,6 +193,19 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Drop the L2 copy of a scratch range of this CTA without writing it back to
+// DRAM (discard.global.L2 on whole 128-byte lines; the contents become undefined).
+// The range is data the tile no longer needs (the layer stores of the gradient
+// sweep, re-written before the next read), so its dirty lines would otherwise be
+// written back to DRAM for nothing.  Call with all threads of the CTA, after a
+// barrier that follows every read of the range; `base` and `bytes` are multiples
+// of 128.
+__device__ __forceinline__ void l2_discard(const void *base, size_t bytes) {
+  const char *b = static_cast<const char *>(base);
+  for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(b + o) : "memory");
+}
+
 // tanh jet: value, first, second, third derivative (tanhf, not an approximation).
 __device__ __forceinline__ void tanh_d(float a, float &z, float &d1, float &d2) {
   z = tanhf(a);
