@@ -421,14 +421,6 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
     const float *Vh = Uh + RH * RM + RH;
     const float *sl = s_s + l * RM;
     const int nr = p.rh[l];
-    // the layer's input jet (unscaled), live through both passes
-    Jet<C, RM> y;
-    if (l > 0) {
-      load_staged<RM, C>(q_b, NT, tid, y);
-      if (l > 1) prefetch_input<RM, C>(l - 1, q_g, q_b, NT, tid);
-    } else {
-      input_jet<RM, C>(V0, x, t, y);
-    }
     const float4 *al = a_g + (size_t)l * RH * NT;
     if (l == L - 1) layer_bwd<RM, C, 1>(Vh, nr, al, qb, ab_s, NT);
     else layer_bwd<RM, C, RM>(Vh, nr, al, qb, ab_s, NT);
@@ -436,6 +428,16 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
     jet_zero<RM, C>(pb);
     if (l == 0) layer_bwd_pbar<RM, C, R1>(Uh, nr, ab_s, NT, pb);
     else layer_bwd_pbar<RM, C, RM>(Uh, nr, ab_s, NT, pb);
+    // the layer's input jet (unscaled), read only now so that it is not live through
+    // the two passes (no spills at 255 registers); then the next layer's input jet
+    // is prefetched into the staging buffer
+    Jet<C, RM> y;
+    if (l > 0) {
+      load_staged<RM, C>(q_b, NT, tid, y);
+      if (l > 1) prefetch_input<RM, C>(l - 1, q_g, q_b, NT, tid);
+    } else {
+      input_jet<RM, C>(V0, x, t, y);
+    }
     // dL/ds^l = sum_c pbar_c * zhat_c and the dL/dbhat^l rows
     float g[RM + RH];
 #pragma unroll

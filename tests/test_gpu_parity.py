@@ -181,6 +181,55 @@ def test_fast_fp32_ragged_instances(P):
         assert rel(dbb[i].cpu(), rb[i]) < TOL_FP32, i
 
 
+def test_fast_many_ragged_instances_with_empty_ones(P):
+    """About 110 tiles of 27 instances, several without points (first, middle, last),
+    so that the per-tile partial rows of neighbouring instances interleave in the
+    reduction and some instances have no tile at all.  Loss and gradient per
+    instance against the oracle on two calls in a row, then two Adam steps."""
+    g = synth.rng(41)
+    net = synth.make_net(g, L=3, M=48, r=16)
+    n = 27
+    n_int = g.integers(0, 700, size=n)
+    n_ic = g.integers(0, 60, size=n)
+    n_bc = g.integers(0, 40, size=n)
+    for i in (0, 9, 10, 26):
+        n_int[i] = n_ic[i] = n_bc[i] = 0
+    bt = as_f32_batch(synth.make_batch(g, net, n_int, n_ic, n_bc, g.uniform(1, 20, n),
+                                       g.uniform(0, 5, n), g.uniform(0, 5, n)))
+    rows, Xis, _ = eim_for(net, bt.s[0], 16)
+    fnet = lrnr64.make_fast(net, rows, Xis)
+    model, db = make(P, net, bt)
+    install_fast(P, model, rows, Xis)
+    ro, rs, rb = lrnr64.residual_grad(fnet, bt, "fast")
+    for rep in range(2):   # tickets must be back at zero for the second call
+        lo, ds, dbb = P.lrnr_residual_grad(model, "fast", "fp32", db)
+        for i in range(n):
+            if n_int[i] + n_ic[i] + n_bc[i] == 0:
+                assert lo[i].item() == 0.0 and torch.all(ds[i] == 0) and torch.all(dbb[i] == 0)
+                continue
+            assert abs(lo[i].item() - ro[i]) <= TOL_FP32 * abs(ro[i]), (rep, i)
+            assert rel(ds[i].cpu(), rs[i]) < TOL_FP32, (rep, i)
+            assert rel(dbb[i].cpu(), rb[i]) < TOL_FP32, (rep, i)
+    s = torch.tensor(bt.s, dtype=torch.float32, device="cuda")
+    m = torch.zeros_like(s)
+    v = torch.zeros_like(s)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lo = torch.zeros(n, dtype=torch.float32, device="cuda")
+    P.spinprop_step(model, "fast", "fp32", db, s, m, v, step, n_steps=2, lr=1e-2, loss_out=lo)
+    assert step.item() == 2
+    for i in range(n):
+        inst = bt.instance(i)
+
+        def lg(sv, inst=inst):
+            d = dict(inst)
+            d["s"] = sv
+            l_, g_, _ = lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet, d)
+            return l_, g_
+        sr, _, _, _ = adam64.spinprop_loop(lg, inst["s"], 2, lr=1e-2)
+        disp = max(np.abs(sr - inst["s"]).max(), 1e-30)
+        assert np.max(np.abs(s[i].cpu().numpy() - sr)) <= 1e-3 * disp + 1e-6, i
+
+
 def test_fast_equals_full_when_every_row_is_kept(P):
     g = synth.rng(31)
     net = synth.make_net(g, L=3, M=16, r=8)
