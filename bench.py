@@ -359,7 +359,80 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
         cmp[form] = {"steps_per_s": 199e3 / e0.elapsed_time(e1), "loss_first_step": l0,
                      "final_full_lrnr_loss": float(lf.mean())}
     out["spinprop_fast_vs_full_16_instances"] = cmp
+    del model, db, dsub
+    out["paper_d1_fast_phase"] = paper_fast_phase(P, synth, np, torch, dev)
     return out
+
+
+def paper_fast_phase(P, synth, np, torch, dev):
+    """The fast phase on the paper's convection architecture in shape (M = 4,000,
+    r = (1, 5, 5, 3, 1), rhat = 5, X = 12 points, l1 loss + locality, Adam), against a
+    full-width fine-tune Adam step (MSE over 69,632 collocation points), both FP32
+    and graph-captured; the paper quotes 0.004 s vs 0.14 s per step on a V100 for its
+    rank-49 architecture (context only)."""
+    from paper_2410_04001_gb300 import fastphase
+    net, bx, bt = synth.workload_paper_d1()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    g = synth.rng(77)
+    xs, ts = synth.snapshot_design(g, 8)
+    s0 = bx.s[0]
+    draws = np.stack([s0] + [s0 * (1.0 + 0.1 * g.standard_normal(s0.shape)) for _ in range(7)])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fastphase.build_reduced(model, torch.tensor(xs, device=dev), torch.tensor(ts, device=dev),
+                            torch.tensor(draws, device=dev), rhat=5)
+    e1.record()
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    dX = P.DeviceBatch.from_host(bx, dev)
+    dT = P.DeviceBatch.from_host(bt, dev)
+    res = {"workload": "M=4000, r=(1,5,5,3,1), convection beta=7; fast phase on the 12-point "
+                       "4x3 grid (l1 + locality 1e-3, lr 1e-3); fine-tune on 65,536 + 2,048 + "
+                       "1,024 pairs (MSE)", "build_reduced_ms": build_ms}
+
+    def step_time(form, batch, loss, lam, reps=200, prec="fp32"):
+        s = batch.s.clone()
+        anchor = s.clone()
+        m, v = torch.zeros_like(s), torch.zeros_like(s)
+        k = torch.zeros(1, dtype=torch.int64, device=dev)
+        lo = torch.zeros(1, dtype=torch.float32, device=dev)
+        fn = lambda: P.spinprop_step(model, form, prec, batch, s, m, v, k, 1, lr=1e-3,
+                                     lambda_loc=lam, s_anchor=anchor, loss=loss, loss_out=lo)
+        for _ in range(3):
+            fn()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, capture_error_mode="relaxed"):
+            fn()
+        for _ in range(3):
+            gr.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            gr.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / reps
+
+    fast_us = step_time("fast", dX, "l1", 1e-3)
+    full_us = step_time("full", dT, "mse", 0.0, reps=20)
+    try:
+        full_bf16_us = step_time("full", dT, "mse", 0.0, reps=20, prec="bf16")
+    except P.LrnrError as e:
+        full_bf16_us = str(e)
+    # the whole fast phase: 400 Adam steps (the paper's epoch budget) in one call
+    e0.record()
+    s_fast = fastphase.fast_phase(model, dX, 400, lr=1e-3, lambda_loc=1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    lf0, _, _ = P.lrnr_residual_grad(model, "full", "fp32", dT, want_db=False)
+    lf1, _, _ = P.lrnr_residual_grad(model, "full", "fp32", dT.with_s(s_fast), want_db=False)
+    res.update({"fast_step_us": fast_us, "full_finetune_step_us": full_us,
+                "full_finetune_step_bf16_us": full_bf16_us,
+                "full_over_fast_step_ratio": full_us / fast_us,
+                "fast_phase_400_steps_ms": e0.elapsed_time(e1),
+                "finetune_loss_at_s0": float(lf0[0]), "finetune_loss_at_s_fast": float(lf1[0]),
+                "s_fast_minus_s0_max": float((s_fast - dX.s).abs().max())})
+    return res
 
 # --------------------------------------------------------------------------- our arm
 

@@ -103,6 +103,24 @@ def make_net(g: np.random.Generator, L: int, M: int, r: int, r1: int | None = No
     return Net(L=L, M=M, r=rk, U=U, V=V, b=b)
 
 
+def make_net_ranks(g: np.random.Generator, M: int, rk) -> Net:
+    """Random bases with explicit ranks ``rk`` (L+1 entries, input layer first),
+    drawn so that each layer's product U diag(s) V^T preserves the variance of its
+    input: V ~ N(0, 1/M_in) (fan-in of V^T z) and U ~ N(0, 1/r_l) (fan-in of U p);
+    b ~ N(0, 0.1).  (With U and V both N(0, 1/M), a wide network with rank-5 layers
+    is close to a constant function: its derivative jets shrink by about r/M per
+    layer and the PDE residual vanishes.)"""
+    rk = [int(v) for v in rk]
+    L = len(rk) - 1
+    widths = [2] + [M] * L + [1]
+    U, V, b = [], [], []
+    for l in range(L + 1):
+        U.append(g.normal(0.0, 1.0 / math.sqrt(rk[l]), size=(widths[l + 1], rk[l])))
+        V.append(g.normal(0.0, 1.0 / math.sqrt(widths[l]), size=(widths[l], rk[l])))
+        b.append(g.normal(0.0, math.sqrt(0.1), size=(widths[l + 1],)))
+    return Net(L=L, M=M, r=rk, U=U, V=V, b=b)
+
+
 def make_s(g: np.random.Generator, n_inst: int, sum_r: int) -> np.ndarray:
     return g.uniform(0.5, 1.5, size=(n_inst, sum_r))
 
@@ -191,6 +209,25 @@ def workload_spinprop(n_inst: int = 1024, per_inst: int = 16384):
     net = make_net(g, L=5, M=512, r=16)
     bt = make_instances(g, net, n_inst, per_inst, per_inst, fixed_count=per_inst)
     return net, bt
+
+
+def workload_paper_d1(M: int = 4000, n_tune: int = 65536, beta: float = 7.0):
+    """The paper's convection setting in shape: LRNR of width M = 4,000 with ranks
+    r = (1, 5, 5, 3, 1) (four hidden layers), pure convection with beta = 7; the fast
+    phase samples X = the 4 x 3 cell-centred grid (12 interior points) and the
+    fine-tune phase the collocation batch (n_tune interior, n_tune/32 initial,
+    n_tune/64 periodic pairs).  Returns (net, batch_X, batch_tune)."""
+    g = rng(1005)
+    net = make_net_ranks(g, M, [1, 5, 5, 3, 1])
+    s = make_s(g, 1, net.sum_r)
+    gx = TWO_PI * (np.arange(4) + 0.5) / 4.0
+    gt = (np.arange(3) + 0.5) / 3.0
+    X, T = np.meshgrid(gx, gt, indexing="ij")
+    bx = Batch(beta=np.array([beta]), nu=np.zeros(1), rho=np.zeros(1), s=s.copy(),
+               int_off=_offsets([12]), ic_off=_offsets([0]), bc_off=_offsets([0]),
+               x_int=X.ravel(), t_int=T.ravel(), x_ic=np.zeros(0), t_bc=np.zeros(0))
+    bt = make_batch(g, net, n_tune, n_tune // 32, n_tune // 64, beta, 0.0, 0.0, s=s.copy())
+    return net, bx, bt
 
 
 def snapshot_design(g: np.random.Generator, n_per_point: int = 8, std: float = 0.05):
