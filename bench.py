@@ -672,7 +672,9 @@ def main():
             "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": "points/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "note": "pinned host -> device inputs and s, spinprop_step, loss and s back to host"},
-            "gpu_launches": 3 * args.steps,
+            # per SPInProp step: the FastLRNR kernel (it computes its own tile schedule
+            # for up to 4,096 instances) and the fixed-order reduction + Adam kernel
+            "gpu_launches": 2 * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
             "device_status": status,
