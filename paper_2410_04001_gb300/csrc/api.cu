@@ -64,7 +64,8 @@ struct lrnr_model {
   // launch-shape overrides per (form, precision): points per tile, CTAs per SM cap
   int tune_nt[2][4] = {{0}};
   int tune_cta[2][4] = {{0}};
-  // per-instance tickets of the two-level Adam reduction (zero between calls)
+  // tickets of the two-level Adam reduction and of the FastLRNR kernel's fused
+  // reduction (zero between calls; every ticket is reset by the CTA completing it)
   int *adam_cnt = nullptr;
   int adam_cnt_n = 0;
 };
@@ -105,7 +106,7 @@ bool capturing(cudaStream_t st) {
 }
 
 // Available (RM, RH) instantiations of the FastLRNR kernel, cheapest first.
-const int kFastPairs[][2] = {{8, 16}, {16, 16}};
+const int kFastPairs[][2] = {{8, 8}, {16, 8}, {8, 16}, {16, 16}};
 
 int64_t max_tiles(int64_t n_int, int64_t n_ic, int64_t n_bc, int n_inst, int nt) {
   return (n_int + nt - 1) / nt + (n_ic + nt - 1) / nt + (n_bc + nt / 2 - 1) / (nt / 2) +
@@ -125,6 +126,24 @@ lrnr_status ensure_ws(lrnr_model *m, size_t need, cudaStream_t st) {
   }
   CK(cudaMalloc(&m->ws, need));
   m->ws_bytes = need;
+  return LRNR_OK;
+}
+
+// Zeroed ticket counters, at least n of them (grown outside stream capture only).
+lrnr_status ensure_tickets(lrnr_model *m, int64_t n, cudaStream_t st) {
+  if (m->adam_cnt_n >= n) return LRNR_OK;
+  if (capturing(st)) return LRNR_ENOTREADY;
+  if (n > INT32_MAX) return LRNR_EINVAL;
+  if (m->adam_cnt) {
+    if (st) CK(cudaStreamSynchronize(st));
+    else CK(cudaDeviceSynchronize());
+    CK(cudaFree(m->adam_cnt));
+    m->adam_cnt = nullptr;
+    m->adam_cnt_n = 0;
+  }
+  CK(cudaMalloc(&m->adam_cnt, sizeof(int) * (size_t)n));
+  CK(cudaMemset(m->adam_cnt, 0, sizeof(int) * (size_t)n));
+  m->adam_cnt_n = (int)n;
   return LRNR_OK;
 }
 
@@ -277,17 +296,41 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
     if (grad) scr_bytes = full_fp32_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap) * sizeof(float);
   }
+  // Batches whose tiles fit in one round of the FastLRNR grid (2 CTAs per SM) are
+  // reduced inside the kernel (group rows + tickets): one launch instead of two.
+  const bool fused_red = grad && form == LRNR_FAST && tiles <= 2 * (int64_t)m->num_sms;
+  if (fused_red) {
+    p.fast_regs = 2;
+    ps.grid_cap = (int)std::min<int64_t>(tiles, 2 * (int64_t)m->num_sms);
+    scr_bytes = fast_scratch_floats(m->L, p.RM, p.RH, p.nt, ps.grid_cap) * sizeof(float);
+  }
+  const int64_t n_groups = (tiles + kRedGroup - 1) / kRedGroup;
   const size_t off_part = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));
   const size_t part_bytes = grad ? align256((size_t)tiles * p.P * sizeof(float)) : 0;
   const size_t scr_al = align256(scr_bytes);
-  const size_t adam_bytes = adam ? adam_group_floats(bt->n_inst, m->L, p.RM) * sizeof(float) : 0;
-  rc = ensure_ws(m, off_part + part_bytes + scr_al + adam_bytes, st);
+  const size_t adam_bytes =
+      adam && !fused_red ? align256(adam_group_floats(bt->n_inst, m->L, p.RM) * sizeof(float)) : 0;
+  const size_t gpart_bytes =
+      fused_red ? align256((size_t)(n_groups + bt->n_inst) * p.P * sizeof(float)) : 0;
+  rc = ensure_ws(m, off_part + part_bytes + scr_al + adam_bytes + gpart_bytes, st);
   if (rc != LRNR_OK) return rc;
-  p.tile_off = reinterpret_cast<int32_t *>(m->ws);
-  p.partial = reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part);
-  p.scratch = scr_bytes ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes) : nullptr;
-  ps.gsum = adam ? reinterpret_cast<float *>(static_cast<char *>(m->ws) + off_part + part_bytes + scr_al)
-                 : nullptr;
+  if (fused_red || adam) {
+    rc = ensure_tickets(m, fused_red ? n_groups + bt->n_inst + 1 : bt->n_inst, st);
+    if (rc != LRNR_OK) return rc;
+  }
+  char *ws = static_cast<char *>(m->ws);
+  p.tile_off = reinterpret_cast<int32_t *>(ws);
+  p.partial = reinterpret_cast<float *>(ws + off_part);
+  p.scratch = scr_bytes ? reinterpret_cast<float *>(ws + off_part + part_bytes) : nullptr;
+  ps.gsum = adam_bytes ? reinterpret_cast<float *>(ws + off_part + part_bytes + scr_al) : nullptr;
+  if (fused_red) {
+    p.fused_red = 1;
+    p.n_groups = (int)n_groups;
+    p.gpart = reinterpret_cast<float *>(ws + off_part + part_bytes + scr_al + adam_bytes);
+    p.tickets = m->adam_cnt;
+    p.rows = m->rows_dev;
+    p.sum_m = m->sum_m;
+  }
   p.max_wait = 1u << 20;
   p.loss = LRNR_LOSS_MSE;
   p.w[0] = p.w[1] = p.w[2] = 1.0f;
@@ -598,9 +641,15 @@ lrnr_status lrnr_residual_grad(lrnr_model *m, lrnr_form form, lrnr_precision pre
   if (rc != LRNR_OK) return rc;
   ps.p.loss = loss;
   if (w) { ps.p.w[0] = w[0]; ps.p.w[1] = w[1]; ps.p.w[2] = w[2]; }
+  if (dL_db) CK(cudaMemsetAsync(dL_db, 0, sizeof(float) * (size_t)bt->n_inst * m->sum_m, st));
+  if (ps.p.fused_red) {
+    ps.p.loss_out = loss_out;
+    ps.p.dL_ds = dL_ds;
+    ps.p.dL_db = dL_db;
+    return run_main(m, form, prec, ps, st);
+  }
   rc = run_main(m, form, prec, ps, st);
   if (rc != LRNR_OK) return rc;
-  if (dL_db) CK(cudaMemsetAsync(dL_db, 0, sizeof(float) * (size_t)bt->n_inst * m->sum_m, st));
   const int DB0 = partial_db0(m->L, ps.p.RM);
   const int n_needed = dL_db ? ps.p.P : DB0;
   CK(launch_reduce(ps.p, n_needed, form == LRNR_FAST, m->rows_dev, ps.p.RH, loss_out, dL_ds,
@@ -623,21 +672,28 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec, co
   Pass ps;
   lrnr_status rc = prepare(m, form, prec, bt, true, s_inout, st, ps, true);
   if (rc != LRNR_OK) return rc;
-  if (m->adam_cnt_n < bt->n_inst) {
-    if (capturing(st)) return LRNR_ENOTREADY;
-    if (m->adam_cnt) {
-      CK(cudaStreamSynchronize(st));
-      CK(cudaFree(m->adam_cnt));
-      m->adam_cnt = nullptr;
-      m->adam_cnt_n = 0;
-    }
-    CK(cudaMalloc(&m->adam_cnt, sizeof(int) * (size_t)bt->n_inst));
-    CK(cudaMemset(m->adam_cnt, 0, sizeof(int) * (size_t)bt->n_inst));
-    m->adam_cnt_n = bt->n_inst;
-  }
   ps.p.loss = loss;
   if (w) { ps.p.w[0] = w[0]; ps.p.w[1] = w[1]; ps.p.w[2] = w[2]; }
   ps.p.step = step;
+  if (ps.p.fused_red) {
+    // one kernel per step: residual, adjoint, reduction and Adam
+    KParams &p = ps.p;
+    p.loss_out = loss_out;
+    p.adam_s = s_inout;
+    p.adam_m = adam_m;
+    p.adam_v = adam_v;
+    p.lr = lr;
+    p.b1 = beta1;
+    p.b2 = beta2;
+    p.eps = eps;
+    p.lam = s_anchor ? lambda_loc : 0.0f;
+    p.anchor = s_anchor;
+    for (int k = 0; k < n_steps; ++k) {
+      rc = run_main(m, form, prec, ps, st);
+      if (rc != LRNR_OK) return rc;
+    }
+    return LRNR_OK;
+  }
   for (int k = 0; k < n_steps; ++k) {
     rc = run_main(m, form, prec, ps, st);
     if (rc != LRNR_OK) return rc;
@@ -711,15 +767,10 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) +
                       align256((size_t)tiles * Pmax * sizeof(float)) +
                       align256(store * sizeof(float)) +
-                      adam_group_floats(max_inst, m->L, RMAX) * sizeof(float);
-  if (m->adam_cnt_n < max_inst) {
-    if (m->adam_cnt) CK(cudaFree(m->adam_cnt));
-    m->adam_cnt = nullptr;
-    m->adam_cnt_n = 0;
-    CK(cudaMalloc(&m->adam_cnt, sizeof(int) * (size_t)max_inst));
-    CK(cudaMemset(m->adam_cnt, 0, sizeof(int) * (size_t)max_inst));
-    m->adam_cnt_n = max_inst;
-  }
+                      align256(adam_group_floats(max_inst, m->L, RMAX) * sizeof(float)) +
+                      align256((size_t)(tiles / kRedGroup + 1 + max_inst) * Pmax * sizeof(float));
+  lrnr_status rc = ensure_tickets(m, tiles / kRedGroup + 2 + 2 * (int64_t)max_inst, nullptr);
+  if (rc != LRNR_OK) return rc;
   return ensure_ws(m, need, nullptr);
 }
 

@@ -31,7 +31,7 @@ namespace lrnr {
 // partial row per warp and, when the kernel computes the tile schedule, the tile
 // offsets.
 struct FastLayout {
-  int pack, s, us, ab, qb, red, toff, scan, total;
+  int pack, s, us, ab, qb, red, toff, scan, misc, total;
   __host__ __device__ FastLayout(int L, int RM, int RH, int NT, int P, int fused_inst = 0) {
     pack = 0;
     s = (fast_pack_floats(L, RM, RH) + 3) & ~3;
@@ -41,7 +41,8 @@ struct FastLayout {
     red = qb + 4 * RM * NT;
     toff = red + (NT / 32) * P;
     scan = toff + (fused_inst ? fused_inst + 1 : 0);
-    total = scan + (fused_inst ? NT : 0);
+    misc = scan + (fused_inst ? NT : 0);   // per-warp sums and a flag of the fused reduction
+    total = misc + NT / 32 + 4;
   }
 };
 
@@ -460,9 +461,158 @@ __device__ void fast_tile(const KParams &p, const Tile &T, const float *__restri
   }
 }
 
+// --- fixed-order reduction inside the kernel (KParams::fused_red) ------------------
+
+// Instance owning tile t: the largest i with toff[i] <= t.
+__device__ __forceinline__ int instance_of_tile(const int32_t *toff, int n_inst, int t) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (toff[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Entry j summed over rows a..b-1 of a row matrix with row length P, in row order.
+// The rows were written by other CTAs, so they are read through L2; the loads of a
+// chunk of up to kRedGroup rows are all issued before the additions.
+__device__ __forceinline__ float rows_sum(const float *src, int P, int j, int a, int b) {
+  float acc = 0.0f;
+  for (int c = a; c < b; c += kRedGroup) {
+    float v[kRedGroup];
+#pragma unroll
+    for (int k = 0; k < kRedGroup; ++k)
+      v[k] = (c + k < b) ? __ldcg(src + (int64_t)(c + k) * P + j) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < kRedGroup; ++k) acc += v[k];
+  }
+  return acc;
+}
+
+// Finish instance i: add its group rows in group order, then either write loss,
+// dL/ds and dL/db (scattered to the EIM rows; dL/db zeroed beforehand by the host),
+// or apply Adam to the instance's s (Sec. 4) with the l1 locality subgradient of
+// Eq. 3.7 and write the loss.  An instance without tiles has a zero gradient.  In
+// Adam mode the CTA finishing the last instance advances the step counter.  All
+// threads of the CTA; `buf` holds P floats, `wsum` NT/32 floats (shared memory).
+static __device__ void fast_finish_instance(const KParams &p, int i, const int32_t *toff,
+                                            float *buf, float *wsum, int64_t kstep) {
+  const int tid = threadIdx.x, NT = blockDim.x, P = p.P;
+  const int t0 = toff[i], t1 = toff[i + 1];
+  for (int j = tid; j < P; j += NT)
+    buf[j] = t1 > t0 ? rows_sum(p.gpart, P, j, t0 / kRedGroup + i, (t1 - 1) / kRedGroup + i + 1)
+                     : 0.0f;
+  __syncthreads();
+  const int DB0 = partial_db0(p.L, p.RM);
+  if (!p.adam_s) {
+    for (int j = tid; j < P; j += NT) {
+      const float v = buf[j];
+      if (j == 0) {
+        if (p.loss_out) p.loss_out[i] = v;
+      } else if (j < DB0) {
+        const int l = (j - 1) / p.RM, k = (j - 1) % p.RM;
+        if (k < p.r[l]) p.dL_ds[(int64_t)i * p.sum_r + p.roff[l] + k] = v;
+      } else if (p.dL_db) {
+        const int jj = j - DB0;
+        float *db = p.dL_db + (int64_t)i * p.sum_m;
+        if (jj == p.L * p.RH) {
+          db[p.L * p.M] = v;
+        } else if (jj < p.L * p.RH) {
+          const int row = p.rows[jj];   // [l][RH]: jj = l * RH + slot
+          if (row >= 0) db[(jj / p.RH) * p.M + row] = v;
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const float bc1 = 1.0f - powf(p.b1, (float)kstep);
+  const float bc2 = 1.0f - powf(p.b2, (float)kstep);
+  float loc = 0.0f;
+  for (int j = 1 + tid; j < DB0; j += NT) {
+    const int l = (j - 1) / p.RM, k = (j - 1) % p.RM;
+    if (k >= p.r[l]) continue;
+    const int64_t o = (int64_t)i * p.sum_r + p.roff[l] + k;
+    const float sv = p.adam_s[o];
+    float gr = buf[j];
+    if (p.anchor) {
+      const float d = sv - p.anchor[o];
+      loc += p.lam * fabsf(d);
+      gr += p.lam * (float)((d > 0.0f) - (d < 0.0f));
+    }
+    const float mv = p.b1 * p.adam_m[o] + (1.0f - p.b1) * gr;
+    const float vv = p.b2 * p.adam_v[o] + (1.0f - p.b2) * gr * gr;
+    p.adam_m[o] = mv;
+    p.adam_v[o] = vv;
+    p.adam_s[o] = sv - p.lr * (mv / bc1) / (sqrtf(vv / bc2) + p.eps);
+  }
+  loc = warp_sum(loc);
+  if ((tid & 31) == 0) wsum[tid >> 5] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    float lt = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) lt += wsum[w];
+    if (p.loss_out) p.loss_out[i] = buf[0] + lt;
+    __threadfence();
+    int *tk = p.tickets + p.n_groups + p.n_inst;
+    if (atomicAdd(tk, 1) == p.n_inst - 1) {
+      *tk = 0;
+      *p.step = kstep;
+    }
+  }
+  __syncthreads();
+}
+
+// After a tile's partial row is written (all threads): take the tile's group
+// ticket.  The CTA completing the group sums the group's rows of each instance it
+// holds, in tile order, into that instance's group row gpart[g + i], and takes the
+// instance's ticket; the CTA completing an instance's last group finishes it.
+// Tickets are reset by the CTA that completes them, ready for the next launch.
+static __device__ void fast_tile_done(const KParams &p, int tile, int ntiles, const int32_t *toff,
+                                      float *buf, float *wsum, int *flag, int64_t kstep) {
+  const int tid = threadIdx.x, NT = blockDim.x, P = p.P;
+  const int g = tile / kRedGroup;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const int gsize = min(kRedGroup, ntiles - g * kRedGroup);
+    const int last = atomicAdd(p.tickets + g, 1) == gsize - 1;
+    if (last) p.tickets[g] = 0;
+    flag[0] = last;
+  }
+  __syncthreads();
+  if (!flag[0]) return;
+  __threadfence();
+  const int ta = g * kRedGroup, tb = min(ntiles, ta + kRedGroup);
+  const int i0 = instance_of_tile(toff, p.n_inst, ta);
+  const int i1 = instance_of_tile(toff, p.n_inst, tb - 1);
+  for (int i = i0; i <= i1; ++i) {
+    const int a = max(ta, toff[i]), b = min(tb, toff[i + 1]);
+    if (a >= b) continue;   // an instance without tiles (finished at kernel start)
+    for (int j = tid; j < P; j += NT)
+      p.gpart[(int64_t)(g + i) * P + j] = rows_sum(p.partial, P, j, a, b);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const int ng = (toff[i + 1] - 1) / kRedGroup - toff[i] / kRedGroup + 1;
+      const int last = atomicAdd(p.tickets + p.n_groups + i, 1) == ng - 1;
+      if (last) p.tickets[p.n_groups + i] = 0;
+      flag[0] = last;
+    }
+    __syncthreads();
+    if (flag[0]) {
+      __threadfence();
+      fast_finish_instance(p, i, toff, buf, wsum, kstep);
+    }
+    __syncthreads();
+  }
+}
+
 // MINB: resident CTAs per SM the register allocation is built for (3: at most 168
 // registers per thread; 2: up to 255 registers, no spills).
-template <int RM, int RH, int MINB>
+// FR: the variant with the fixed-order reduction (and Adam) inside the kernel; a
+// separate instantiation, so that the kernel for large batches carries none of it.
+template <int RM, int RH, int MINB, bool FR>
 __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KParams p) {
   static_assert(RH % RB == 0, "row blocks");
   extern __shared__ __align__(16) float smem[];
@@ -481,7 +631,12 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
   float4 *a_g = reinterpret_cast<float4 *>(store + fast_input_store_floats(L, RM, NT));
   const int npack = fast_pack_floats(L, RM, RH);
   for (int i = tid; i < npack; i += NT) w_s[i] = __ldg(p.pack + i);
-  if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
+  // Adam step number: the fused reduction reads the counter here and advances it
+  // once every instance is done; otherwise block 0 advances it for the next kernel
+  if (!FR && p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
+  const int64_t kstep = (FR && p.step) ? *p.step + 1 : 0;
+  float *wsum = smem + lay.misc;
+  int *flag = reinterpret_cast<int *>(smem + lay.misc + NT / 32);
   const int32_t *toff = p.tile_off;
   if (p.fused_tiles) {
     int32_t *toff_s = reinterpret_cast<int32_t *>(smem + lay.toff);
@@ -489,6 +644,11 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
     toff = toff_s;
   }
   const int ntiles = p.fused_tiles ? toff[p.n_inst] : __ldg(p.tile_off + p.n_inst);
+  if constexpr (FR) {
+    // instances without points have no tile: finish them here
+    for (int i = blockIdx.x; i < p.n_inst; i += gridDim.x)
+      if (toff[i] == toff[i + 1]) fast_finish_instance(p, i, toff, red_s, wsum, kstep);
+  }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const Tile T = decode_tile(p, tile, toff);
     __syncthreads();
@@ -522,19 +682,20 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
       }
       // every read of the layer stores is behind the barrier above
       l2_discard(store, fast_store_floats(L, RM, RH, NT) * sizeof(float));
+      if constexpr (FR) fast_tile_done(p, tile, ntiles, toff, red_s, wsum, flag, kstep);
     }
   }
 }
 
-template <int RM, int RH, int MINB>
+template <int RM, int RH, int MINB, bool FR>
 cudaError_t launch_fast_v(const KParams &p, int grid_cap, cudaStream_t st) {
   const int NT = p.nt;
   const FastLayout lay(p.L, RM, RH, NT, p.P, p.fused_tiles ? p.n_inst : 0);
   const size_t bytes = (size_t)lay.total * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_fast<RM, RH, MINB>,
+  cudaError_t e = cudaFuncSetAttribute(k_fast<RM, RH, MINB, FR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_fast<RM, RH, MINB><<<std::max(1, grid_cap), NT, bytes, st>>>(p);
+  k_fast<RM, RH, MINB, FR><<<std::max(1, grid_cap), NT, bytes, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -542,11 +703,11 @@ template <int RM, int RH, int MINB>
 int fast_ctas_per_sm_v(const KParams &p) {
   const FastLayout lay(p.L, RM, RH, p.nt, p.P, p.fused_tiles ? p.n_inst : 0);
   const size_t bytes = (size_t)lay.total * sizeof(float);
-  if (cudaFuncSetAttribute(k_fast<RM, RH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_fast<RM, RH, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes) != cudaSuccess)
     return 1;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<RM, RH, MINB>, p.nt, bytes) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<RM, RH, MINB, false>, p.nt, bytes) !=
       cudaSuccess)
     return 1;
   return std::max(1, per_sm);
@@ -556,8 +717,9 @@ int fast_ctas_per_sm_v(const KParams &p) {
 // SM, some spills), else the 255-register build (2 CTAs per SM).
 template <int RM, int RH>
 cudaError_t launch_fast_t(const KParams &p, int grid_cap, cudaStream_t st) {
-  return p.fast_regs == 3 ? launch_fast_v<RM, RH, 3>(p, grid_cap, st)
-                          : launch_fast_v<RM, RH, 2>(p, grid_cap, st);
+  if (p.fused_red) return launch_fast_v<RM, RH, 2, true>(p, grid_cap, st);
+  return p.fast_regs == 3 ? launch_fast_v<RM, RH, 3, false>(p, grid_cap, st)
+                          : launch_fast_v<RM, RH, 2, false>(p, grid_cap, st);
 }
 
 template <int RM, int RH>

@@ -57,7 +57,26 @@ struct KParams {
   int fused_tiles;             // the tile kernel computes the tile offsets itself
   int fast_regs;               // FastLRNR kernel build: 3 = 168 registers, else 255
   uint32_t max_wait;           // iteration cap of every device-side wait
+  // Fixed-order reduction inside the FastLRNR kernel (fused_red != 0; chosen for
+  // batches whose tiles fit in one round of the grid, where a second launch would
+  // cost more than the reduction).  Tiles form groups of kRedGroup consecutive
+  // tiles; the CTA that completes a group (ticket) sums the group's rows of each
+  // instance in tile order into gpart[g + inst]; the CTA that completes an
+  // instance's last group sums its group rows in order and writes the outputs, or
+  // applies Adam to s when adam_s is set.
+  int fused_red;
+  int n_groups;                // groups of the tile list (host bound)
+  float *gpart;                // [(n_groups + n_inst)][P] group rows
+  int *tickets;                // [n_groups] group, [n_inst] instance, [1] step tickets (zero)
+  const int32_t *rows;         // fast dL/db scatter map [L][RH] (-1 = unused)
+  int sum_m;
+  float *loss_out, *dL_ds, *dL_db;
+  float *adam_s, *adam_m, *adam_v;
+  float lr, b1, b2, eps, lam;
+  const float *anchor;
 };
+
+constexpr int kRedGroup = 32;   // tiles per reduction group
 
 // --- layout of the FP32 packs -------------------------------------------------
 // Fast pack: per hidden layer l: Uh [RH][RM], bh [RH], Vh [RH][RM]; then V^0 [2][R1],
