@@ -571,7 +571,8 @@ def main():
     # ---- variants: full-width FP32 LRNR residual + gradient, fast residual + gradient
     variants = {}
     P.lrnr_timing(model, True)
-    for form, prec in (("full", "fp32"), ("full", "bf16"), ("full", "bf16x3"), ("fast", "fp32")):
+    for form, prec in (("full", "fp32"), ("full", "bf16"), ("full", "bf16x3"), ("fast", "fp32"),
+                       ("fast", "bf16"), ("fast", "bf16x3")):
         try:
             out = P.lrnr_residual_grad(model, form, prec, db)
         except P.LrnrError as e:
@@ -615,7 +616,8 @@ def main():
             assert np.array_equal(p, rows_all[l]), "EIM rows differ from the oracle"
             Xis.append(Xi)
         fnet = lrnr64.make_fast(net, rows_all, Xis)
-        for form, ref, precs in (("fast", fnet, ("fp32",)), ("full", net, ("fp32", "bf16", "bf16x3"))):
+        for form, ref, precs in (("fast", fnet, ("fp32", "bf16", "bf16x3")),
+                                 ("full", net, ("fp32", "bf16", "bf16x3"))):
             ro, rs, rb = lrnr64.residual_grad(ref, bt32, form)
             for prec in precs:
                 if "unavailable" in variants.get(f"{form}_{prec}", {}):

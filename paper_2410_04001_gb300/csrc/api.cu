@@ -18,9 +18,9 @@ cudaError_t launch_snapshots_f64(const double *w64, int L, int M, const int *r_d
                                  const int64_t *offs_dev, int layer, int64_t n_pts,
                                  const double *x, const double *t, int n_s, const double *s,
                                  int sum_r, double *out, cudaStream_t st);
-int full_tc_supported(int L, int M, int RM);
-size_t full_tc_pack_bytes(int L, int M, int RM);
-void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &U,
+int full_tc_supported(int L, int M, int RM, int NC);
+size_t full_tc_pack_bytes(int L, int M, int RM, int NC);
+void full_tc_pack(int L, int M, int RM, int NC, const std::vector<std::vector<double>> &U,
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
                   const int *r, std::vector<unsigned char> &out);
 int full_tc_nt();
@@ -43,6 +43,7 @@ struct lrnr_model {
   int *r_dev = nullptr;
   int64_t *offs_dev = nullptr;
   void *tc_pack = nullptr;                     // tensor-core operand pack (full form)
+  void *ftc_pack = nullptr;                    // tensor-core pack of the reduced network
   // reduced layers (host, FP64): Uh [rh][r_l], bh [rh], Vh [rh][r_{l+1}], rows [rh]
   int rhat[LMAX] = {0};
   std::vector<std::vector<double>> Uh, bh, Vh;
@@ -157,7 +158,13 @@ lrnr_status build_fast_pack(lrnr_model *m) {
   int RMp = 0, RHp = 0;
   for (auto &pr : kFastPairs)
     if (pr[0] >= m->RM && pr[1] >= need_rh) { RMp = pr[0]; RHp = pr[1]; break; }
-  if (!RMp) return LRNR_ENOTSUP;
+  // no FP32 instantiation for these ranks: only the tensor-core form of the reduced
+  // network is built (RM = the model's padded rank)
+  const bool fp32_ok = RMp != 0;
+  if (!fp32_ok) {
+    RMp = m->RM;
+    RHp = need_rh <= 8 ? 8 : (need_rh <= 16 ? 16 : 32);
+  }
   const int L = m->L;
   const int LS = fast_layer_floats(RMp, RHp);
   std::vector<float> pk((size_t)fast_pack_floats(L, RMp, RHp), 0.0f);
@@ -183,12 +190,41 @@ lrnr_status build_fast_pack(lrnr_model *m) {
   if (m->rows_dev) cudaFree(m->rows_dev);
   m->fast_pack = nullptr;
   m->rows_dev = nullptr;
-  CK(cudaMalloc(&m->fast_pack, pk.size() * sizeof(float)));
-  CK(cudaMemcpy(m->fast_pack, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (fp32_ok) {
+    CK(cudaMalloc(&m->fast_pack, pk.size() * sizeof(float)));
+    CK(cudaMemcpy(m->fast_pack, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   CK(cudaMalloc(&m->rows_dev, rw.size() * sizeof(int32_t)));
   CK(cudaMemcpy(m->rows_dev, rw.data(), rw.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   m->fRM = RMp;
   m->fRH = RHp;
+  // The reduced network is itself an LRNR of width RHp with bases (Uhat, Vhat, bhat)
+  // (Eq. 2.8): pack it for the tensor-core kernel in 16-column chunks, rows past
+  // rhat zero (they contribute nothing and get a zero dL/db).
+  if (m->ftc_pack) cudaFree(m->ftc_pack);
+  m->ftc_pack = nullptr;
+  const int RMt = std::max(16, RMp);
+  if (full_tc_supported(L, RHp, RMt, 16)) {
+    std::vector<std::vector<double>> Ur(L + 1), Vr(L + 1), br(L + 1);
+    Vr[0] = m->V[0];
+    Ur[L] = m->U[L];
+    br[L] = m->b[L];
+    for (int l = 0; l < L; ++l) {
+      const int rh = m->rhat[l], rin = m->r[l], rout = m->r[l + 1];
+      Ur[l].assign((size_t)RHp * rin, 0.0);
+      br[l].assign(RHp, 0.0);
+      Vr[l + 1].assign((size_t)RHp * rout, 0.0);
+      for (int a = 0; a < rh; ++a) {
+        for (int k = 0; k < rin; ++k) Ur[l][(size_t)a * rin + k] = m->Uh[l][(size_t)a * rin + k];
+        br[l][a] = m->bh[l][a];
+        for (int k = 0; k < rout; ++k) Vr[l + 1][(size_t)a * rout + k] = m->Vh[l][(size_t)a * rout + k];
+      }
+    }
+    std::vector<unsigned char> tp;
+    full_tc_pack(L, RHp, RMt, 16, Ur, Vr, br, m->r, tp);
+    CK(cudaMalloc(&m->ftc_pack, tp.size()));
+    CK(cudaMemcpy(m->ftc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice));
+  }
   m->fast_dirty = false;
   return LRNR_OK;
 }
@@ -230,10 +266,23 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   p.x_int = bt->x_int; p.t_int = bt->t_int; p.x_ic = bt->x_ic; p.t_bc = bt->t_bc;
   p.grad = grad ? 1 : 0;
   p.status = m->status_dev;
-  if (form == LRNR_FAST) {
+  if (form == LRNR_FAST && (prec == LRNR_BF16 || prec == LRNR_BF16X3)) {
+    // the reduced network on the tensor cores: an LRNR of width RH
+    rc = build_fast_pack(m);
+    if (rc != LRNR_OK) return rc;
+    if (!m->ftc_pack) return LRNR_ENOTSUP;
+    p.RM = std::max(16, m->fRM);
+    p.RH = m->fRH;
+    p.M = m->fRH;
+    for (int l = 0; l < m->L; ++l) p.rh[l] = m->rhat[l];
+    p.pack = nullptr;
+    p.nt = full_tc_nt();
+    ps.nb_entries = m->L * p.RH + 1;
+  } else if (form == LRNR_FAST) {
     if (prec != LRNR_FP32) return LRNR_ENOTSUP;
     rc = build_fast_pack(m);
     if (rc != LRNR_OK) return rc;
+    if (!m->fast_pack) return LRNR_ENOTSUP;   // ranks above the FP32 instantiations
     p.RM = m->fRM;
     p.RH = m->fRH;
     p.pack = m->fast_pack;
@@ -262,7 +311,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
         p.nt = tn;
     } else if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
       p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
-      if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM)) return LRNR_ENOTSUP;
+      if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM, 32)) return LRNR_ENOTSUP;
       p.pack = nullptr;
       p.nt = full_tc_nt();
     } else {
@@ -275,11 +324,12 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   p.P = grad ? partial_len(m->L, p.RM, ps.nb_entries - 1) : 0;
   const int64_t tiles = max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, p.nt);
   if (tiles > INT32_MAX / 2) return LRNR_EINVAL;
-  const bool tc = form == LRNR_FULL && (prec == LRNR_BF16 || prec == LRNR_BF16X3);
+  const bool tc = prec == LRNR_BF16 || prec == LRNR_BF16X3;
   ps.grid_cap = (int)std::min<int64_t>(tiles, INT32_MAX);
   size_t scr_bytes = 0;
   if (tc) {
-    ps.grid_cap = (int)std::min<int64_t>(tiles, m->num_sms);
+    // one CTA per SM with 32-column chunks, two with 16-column chunks (reduced form)
+    ps.grid_cap = (int)std::min<int64_t>(tiles, (form == LRNR_FAST ? 2 : 1) * (int64_t)m->num_sms);
     scr_bytes = full_tc_scratch_floats(m->L, p.RM, ps.grid_cap) * sizeof(float);
   } else if (form == LRNR_FAST) {
     // the FastLRNR kernel keeps layer inputs in a per-CTA scratch: size the grid first
@@ -298,7 +348,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   }
   // Batches whose tiles fit in one round of the FastLRNR grid (2 CTAs per SM) are
   // reduced inside the kernel (group rows + tickets): one launch instead of two.
-  const bool fused_red = grad && form == LRNR_FAST && tiles <= 2 * (int64_t)m->num_sms;
+  const bool fused_red =
+      grad && form == LRNR_FAST && prec == LRNR_FP32 && tiles <= 2 * (int64_t)m->num_sms;
   if (fused_red) {
     p.fast_regs = 2;
     ps.grid_cap = (int)std::min<int64_t>(tiles, 2 * (int64_t)m->num_sms);
@@ -365,12 +416,13 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
     ++m->ev_used;
     CK(cudaEventRecord(e1, st));
   }
-  if (form == LRNR_FAST) {
+  if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
+    const bool fast = form == LRNR_FAST;
+    CK(launch_full_tc(p, fast ? m->ftc_pack : m->tc_pack, (int)prec, fast ? 16 : 32, ps.grid_cap, st));
+  } else if (form == LRNR_FAST) {
     CK(launch_fast(p, ps.grid_cap, st));
-  } else if (prec == LRNR_FP32) {
-    CK(launch_full_fp32(p, ps.grid_cap, st));
   } else {
-    CK(launch_full_tc(p, m->tc_pack, (int)prec, ps.grid_cap, st));
+    CK(launch_full_fp32(p, ps.grid_cap, st));
   }
   if (e2) CK(cap ? cudaEventRecordWithFlags(e2, st, cudaEventRecordExternal) : cudaEventRecord(e2, st));
   return LRNR_OK;
@@ -485,9 +537,9 @@ lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U, const
   if ((e = cudaMemcpy(m->offs_dev, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&m->status_dev, sizeof(int))) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(m->status_dev, 0, sizeof(int))) != cudaSuccess) return fail(e);
-  if (full_tc_supported(L, M, std::max(16, RM))) {
+  if (full_tc_supported(L, M, std::max(16, RM), 32)) {
     std::vector<unsigned char> tp;
-    full_tc_pack(L, M, std::max(16, RM), m->U, m->V, m->b, m->r, tp);
+    full_tc_pack(L, M, std::max(16, RM), 32, m->U, m->V, m->b, m->r, tp);
     if ((e = cudaMalloc(&m->tc_pack, tp.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(m->tc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   }
@@ -652,7 +704,9 @@ lrnr_status lrnr_residual_grad(lrnr_model *m, lrnr_form form, lrnr_precision pre
   if (rc != LRNR_OK) return rc;
   const int DB0 = partial_db0(m->L, ps.p.RM);
   const int n_needed = dL_db ? ps.p.P : DB0;
-  CK(launch_reduce(ps.p, n_needed, form == LRNR_FAST, m->rows_dev, ps.p.RH, loss_out, dL_ds,
+  KParams pr = ps.p;
+  pr.M = m->M;   // dL/db is laid out by the full width (the reduced tensor-core pass ran with M = RH)
+  CK(launch_reduce(pr, n_needed, form == LRNR_FAST, m->rows_dev, pr.RH, loss_out, dL_ds,
                    dL_db, m->sum_m, st));
   return LRNR_OK;
 }
@@ -715,7 +769,8 @@ lrnr_status noalloc_fast_params(lrnr_model *m, const lrnr_batch *bt, lrnr_loss l
   lrnr_status rc = check_batch(m, bt);
   if (rc != LRNR_OK) return rc;
   if (!bt->s) return LRNR_EINVAL;
-  if (m->fast_dirty || !m->fast_pack) return LRNR_ENOTREADY;
+  if (m->fast_dirty) return LRNR_ENOTREADY;
+  if (!m->fast_pack) return LRNR_ENOTSUP;   // ranks above the FP32 instantiations
   std::memset(&p, 0, sizeof(p));
   p.L = m->L;
   p.M = m->M;
@@ -761,7 +816,7 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   int Pmax = partial_len(m->L, m->RM, m->L * m->M + 1);
   Pmax = std::max(Pmax, partial_len(m->L, RMAX, m->L * RHMAX + 1));
   // per-CTA layer-input stores (tensor-core and FastLRNR kernels): at most 4 CTAs per SM
-  const size_t store = std::max(std::max(full_tc_scratch_floats(m->L, RMAX, m->num_sms),
+  const size_t store = std::max(std::max(full_tc_scratch_floats(m->L, RMAX, 2 * m->num_sms),
                                          fast_scratch_floats(m->L, RMAX, RHMAX, 128, 4 * m->num_sms)),
                                 full_fp32_scratch_floats(m->L, RMAX, 64, 8 * m->num_sms));
   const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) +
@@ -858,6 +913,7 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->r_dev);
   cudaFree(m->offs_dev);
   cudaFree(m->tc_pack);
+  cudaFree(m->ftc_pack);
   cudaFree(m->fast_pack);
   cudaFree(m->rows_dev);
   cudaFree(m->status_dev);

@@ -40,13 +40,16 @@ namespace {
 
 constexpr int TNT = 128;   // points per tile = TMEM lanes
 constexpr int NTH = 256;   // threads: two per point (column halves of a chunk)
-constexpr int NC = 32;     // hidden-width chunk
-constexpr int HC = NC / 2; // columns per epilogue thread
+// NC: hidden-width chunk, 32 (full-width networks: one CTA and 512 TMEM columns per
+// SM) or 16 (narrow networks such as the FastLRNR reduced layers: two CTAs and 256
+// TMEM columns each per SM, so that one CTA's epilogue overlaps the other's MMAs).
+template <int NC>
+constexpr int tmem_cols() { return NC == 16 ? 256 : 512; }
 
 // Chunk block of the packed bases (bytes), three equal groups of PIECE bytes: the
 // hi pieces of Ub (NC x RM), Vb (NC x RM), Utb (RM x NC), Vtb (RM x NC) followed by
 // the chunk's biases (NC floats); then the mid pieces; then the lo pieces.
-template <int RM>
+template <int RM, int NC>
 struct Pk {
   static constexpr int T = NC * RM * 2;
   static constexpr int PIECE = 4 * T + 4 * NC;      // offset from a hi tile to its mid tile
@@ -55,12 +58,13 @@ struct Pk {
   static constexpr int CHUNK = ALL;
 };
 
-template <int RM, int PREC>
+template <int RM, int PREC, int NC>
 struct TcLayout {
+  static constexpr int HC = NC / 2;                 // columns per epilogue thread
   static constexpr int PARTS = PREC == 3 ? 2 : 1;   // activation pieces
   static constexpr int A1B = TNT * RM * 2;          // one (channel, piece) rank-r operand
   static constexpr int A24B = TNT * NC * 2;         // one (channel, piece) width operand
-  static constexpr int BBYTES = PREC == 3 ? Pk<RM>::ALL : Pk<RM>::HI;
+  static constexpr int BBYTES = PREC == 3 ? Pk<RM, NC>::ALL : Pk<RM, NC>::HI;
   static constexpr int OFF_A1 = 0;
   static constexpr int OFF_A3 = OFF_A1 + 4 * PARTS * A1B;
   static constexpr int OFF_A24 = OFF_A3 + 4 * PARTS * A1B;
@@ -97,9 +101,9 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
 }
 
 // Write a rank-r row (this thread's point) of channel c into a K-major operand.
-template <int RM, int PREC>
+template <int RM, int PREC, int NC>
 __device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const float *v, int row) {
-  using Lay = TcLayout<RM, PREC>;
+  using Lay = TcLayout<RM, PREC, NC>;
 #pragma unroll
   for (int k0 = 0; k0 < RM; k0 += 8) {
     float w[8];
@@ -116,14 +120,14 @@ __device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const f
 // D (+)= A B^T with A = Ah (+ Al) and B = Bh (+ Bm + Bl) in BF16 pieces.  BF16:
 // Ah Bh.  Split: Ah Bh + Ah Bm + Al Bh + Ah Bl + Al Bm; the dropped terms are below
 // 2^-25 relative, and the error left is that of the two-piece activation.
-template <int RM, int PREC>
+template <int RM, int PREC, int NC>
 __device__ __forceinline__ void mma_split(uint32_t d, uint32_t aHi, uint32_t aLo, uint32_t b,
                                           uint32_t sboA, uint32_t sboB, uint32_t idesc,
                                           uint32_t acc) {
   const uint64_t ah = tc::sdesc(aHi, 128, sboA);
   tc::mma_bf16(d, ah, tc::sdesc(b, 128, sboB), idesc, acc);
   if constexpr (PREC == 3) {
-    constexpr uint32_t PC = Pk<RM>::PIECE;
+    constexpr uint32_t PC = Pk<RM, NC>::PIECE;
     const uint64_t al = tc::sdesc(aLo, 128, sboA);
     const uint64_t bm = tc::sdesc(b + PC, 128, sboB);
     tc::mma_bf16(d, ah, bm, idesc, 1u);
@@ -146,12 +150,13 @@ struct Ctl {
   int chunk_ctr;            // chunks consumed so far (selects the B buffer)
 };
 
-template <int RM, int PREC, int C>
+template <int RM, int PREC, int C, int NC>
 __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char *sm,
                         const unsigned char *__restrict__ pack, float *__restrict__ qst,
                         uint32_t tb, Ctl &ctl, bool &dead) {
-  using Lay = TcLayout<RM, PREC>;
-  using PK = Pk<RM>;
+  using Lay = TcLayout<RM, PREC, NC>;
+  using PK = Pk<RM, NC>;
+  constexpr int HC = NC / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = tid & (TNT - 1);       // point / TMEM lane
   const int half = tid >> 7;             // column half of the epilogue
@@ -177,42 +182,37 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   constexpr uint32_t SBO_R = RM * 16, SBO_W = NC * 16;
 
   const PointIn pt = load_point(p, T, row);
-  float q[C][RM];
-  auto input_jet = [&]() {
+  // Rank-r jets are handled one channel at a time (RM floats live at a time): the
+  // input jet of layer 0, the rank-r accumulator in TMEM, the layer-input store.
+  auto input_jet_c = [&](int c, float (&v)[RM]) {
 #pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < RM; ++k) q[c][k] = 0.0f;
+    for (int k = 0; k < RM; ++k) v[k] = 0.0f;
 #pragma unroll
     for (int k = 0; k < R1; ++k) {
-      q[0][k] = tail[k] * pt.x + tail[R1 + k] * pt.t;
-      if constexpr (C == 4) {
-        q[1][k] = tail[R1 + k];
-        q[2][k] = tail[k];
-      }
+      if (c == 0) v[k] = tail[k] * pt.x + tail[R1 + k] * pt.t;
+      else if (c == 1) v[k] = tail[R1 + k];
+      else if (c == 2) v[k] = tail[k];
     }
   };
-  auto put_A1 = [&](int l) {
+  auto rank_c = [&](int c, float (&v)[RM]) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      float y[RM];
+    for (int k0 = 0; k0 < RM; k0 += 16) {
+      float w[16];
+      tc::tmem_ld16(D24 + lane_base + c * RM + k0, w);
+      tc::tmem_ld_wait();
 #pragma unroll
-      for (int k = 0; k < RM; ++k) y[k] = q[c][k] * s_s[l * RM + k];
-      put_rank_row<RM, PREC>(sA1, c, y, row);
+      for (int i = 0; i < 16; ++i) v[k0 + i] = w[i];
     }
   };
-  auto read_rank = [&](float (&o)[C][RM]) {
+  auto stored_c = [&](int l, int c, float (&v)[RM]) {   // input jet of layer l >= 1
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
+    for (int k = 0; k < RM; ++k) v[k] = qst[(((l - 1) * 4 + c) * RM + k) * TNT + row];
+  };
+  auto put_scaled = [&](unsigned char *base, int c, const float (&v)[RM], int l) {
+    float y[RM];
 #pragma unroll
-      for (int k0 = 0; k0 < RM; k0 += 16) {
-        float v[16];
-        tc::tmem_ld16(D24 + lane_base + c * RM + k0, v);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) o[c][k0 + i] = v[i];
-      }
-    }
+    for (int k = 0; k < RM; ++k) y[k] = v[k] * s_s[l * RM + k];
+    put_rank_row<RM, PREC, NC>(base, c, y, row);
   };
   auto bbuf = [&](int n) { return sB0 + (n % Lay::NB) * Lay::BSTRIDE; };
   // Stream the chunks of a layer through the B buffers: before chunk j, chunk j+1
@@ -223,19 +223,19 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   };
   auto wait_b = [&](int n) { return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], p); };
 
-  // ---------------- forward
-  if (lead) input_jet();
+  // ---------------- forward (the operand A1 of layer l >= 1 is written at the end
+  // of layer l - 1, from its rank-r result)
+  if (lead) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float v[RM];
+      input_jet_c(c, v);
+      put_scaled(sA1, c, v, 0);
+    }
+  }
+  float qL[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // the last layer's rank-1 result, per channel
   for (int l = 0; l < L && !dead; ++l) {
     const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
-    if (lead) {
-      if (p.grad && l > 0) {
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int k = 0; k < RM; ++k) qst[(((l - 1) * 4 + c) * RM + k) * TNT + row] = q[c][k];
-      }
-      put_A1(l);
-    }
     const int n0 = ctl.chunk_ctr;
     fetch(lp, 0, n0);
     for (int j = 0; j < NCH; ++j) {
@@ -253,7 +253,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < RM / 16; ++kk)
-            mma_split<RM, PREC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+            mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
                                 sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
                                 SBO_R, ID_W, kk > 0);
         tc::mma_commit(ctl.b1);
@@ -264,7 +264,10 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         const int c0 = half * HC;
         float a[C][HC];
 #pragma unroll
-        for (int c = 0; c < C; ++c) tc::tmem_ld16(D1 + lane_base + c * NC + c0, a[c]);
+        for (int c = 0; c < C; ++c) {
+          if constexpr (HC == 16) tc::tmem_ld16(D1 + lane_base + c * NC + c0, a[c]);
+          else tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
+        }
         tc::tmem_ld_wait();
 #pragma unroll
         for (int i = 0; i < HC; ++i) {
@@ -300,7 +303,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < NC / 16; ++kk)
-            mma_split<RM, PREC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
+            mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
                                 sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 3 * PK::T + kk * 256,
                                 SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
         tc::mma_commit(ctl.b2);
@@ -308,14 +311,29 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     }
     ctl.chunk_ctr = n0 + NCH;
     if (!wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
-    if (lead) read_rank(q);
+    if (lead) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        float v[RM];
+        rank_c(c, v);
+        if (l + 1 < L) {
+          if (p.grad) {
+#pragma unroll
+            for (int k = 0; k < RM; ++k) qst[((l * 4 + c) * RM + k) * TNT + row] = v[k];
+          }
+          put_scaled(sA1, c, v, l + 1);
+        } else {
+          qL[c] = v[0];
+        }
+      }
+    }
     tc::fence_before_sync();
   }
   float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   const float sL = s_s[L * RM];
   if (lead) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0];
+    for (int c = 0; c < C; ++c) u[c] = Uout * sL * qL[c];
     u[0] += bout;
   }
   float ub[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lpv = 0.0f;
@@ -326,13 +344,12 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   // ---------------- reverse sweep
   const int DB0 = partial_db0(L, RM);
   float *prow = p.partial + (int64_t)tile * p.P;
-  float qb[C][RM];
   if (lead) {
     // loss, dL/ds of the linear output layer, dL/db of the output bias
     const float ls = warp_sum(lpv);
     float dsL = 0.0f;
 #pragma unroll
-    for (int c = 0; c < C; ++c) dsL += Uout * ub[c] * q[c][0];
+    for (int c = 0; c < C; ++c) dsL += Uout * ub[c] * qL[c];
     const float s0 = warp_sum(dsL);
     const float s1 = warp_sum(ub[0]);
     if (lane == 0) {
@@ -340,28 +357,27 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       red_w[1 + L * RM] += s0;
       red_w[PL - 1] += s1;
     }
+    // A3 of the last hidden layer: the output adjoint seeds
 #pragma unroll
     for (int c = 0; c < C; ++c) {
+      float qb[RM];
 #pragma unroll
-      for (int k = 0; k < RM; ++k) qb[c][k] = 0.0f;
-      qb[c][0] = sL * Uout * ub[c];
+      for (int k = 0; k < RM; ++k) qb[k] = 0.0f;
+      qb[0] = sL * Uout * ub[c];
+      put_rank_row<RM, PREC, NC>(sA3, c, qb, row);
     }
   }
+  // (A3 of layer l < L - 1 is written at the end of layer l + 1: pbar * s^(l+1))
   for (int l = L - 1; l >= 0 && !dead; --l) {
     const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
     if (lead) {
-      // qb first: it is dead once written, so q and qb are never live together
 #pragma unroll
-      for (int c = 0; c < C; ++c) put_rank_row<RM, PREC>(sA3, c, qb[c], row);
-      if (l > 0) {
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int k = 0; k < RM; ++k) q[c][k] = qst[(((l - 1) * 4 + c) * RM + k) * TNT + row];
-      } else {
-        input_jet();
+      for (int c = 0; c < C; ++c) {
+        float v[RM];
+        if (l > 0) stored_c(l, c, v);
+        else input_jet_c(c, v);
+        put_scaled(sA1, c, v, l);
       }
-      put_A1(l);
     }
     const int n0 = ctl.chunk_ctr;
     fetch(lp, 0, n0);
@@ -380,10 +396,10 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < RM / 16; ++kk) {
-            mma_split<RM, PREC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+            mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
                                 sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
                                 SBO_R, ID_W, kk > 0);
-            mma_split<RM, PREC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+            mma_split<RM, PREC, NC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
                                 sA3u + (2 * c + 1) * Lay::A1B + kk * 256, sB + PK::T + kk * 256,
                                 SBO_R, SBO_R, ID_W, kk > 0);
           }
@@ -439,7 +455,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < NC / 16; ++kk)
-            mma_split<RM, PREC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
+            mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
                                 sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 2 * PK::T + kk * 256,
                                 SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
         tc::mma_commit(ctl.b2);
@@ -456,44 +472,30 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     ctl.chunk_ctr = n0 + NCH;
     if (!wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
     if (lead) {
-      float pb[C][RM];
-      read_rank(pb);
-      // dL/ds^l = sum_c pbar_c * q_c, reading q element by element
+      // dL/ds^l = sum_c pbar_c * q_c, and the output adjoint of layer l - 1
       float g[RM];
 #pragma unroll
-      for (int k = 0; k < RM; ++k) {
-        float d = 0.0f;
+      for (int k = 0; k < RM; ++k) g[k] = 0.0f;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          float qv;
-          if (l > 0) {
-            qv = qst[(((l - 1) * 4 + c) * RM + k) * TNT + row];
-          } else {
-            qv = 0.0f;
-            if (k < R1) {
-              if (c == 0) qv = tail[k] * pt.x + tail[R1 + k] * pt.t;
-              else if (c == 1) qv = tail[R1 + k];
-              else if (c == 2) qv = tail[k];
-            }
-          }
-          d = fmaf(pb[c][k], qv, d);
-        }
-        g[k] = d;
+      for (int c = 0; c < C; ++c) {
+        float pb[RM], v[RM];
+        rank_c(c, pb);
+        if (l > 0) stored_c(l, c, v);
+        else input_jet_c(c, v);
+#pragma unroll
+        for (int k = 0; k < RM; ++k) g[k] = fmaf(pb[k], v[k], g[k]);
+        if (l > 0) put_scaled(sA3, c, pb, l);
       }
       warp_accumulate<RM>(g, red_w, [&](int jj) { return 1 + l * RM + jj; });
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < RM; ++k) qb[c][k] = pb[c][k] * s_s[l * RM + k];
     }
     tc::fence_before_sync();
   }
 }
 
-template <int RM, int PREC>
-__global__ void __launch_bounds__(NTH, 1) k_full_tc(const __grid_constant__ KParams p,
+template <int RM, int PREC, int NC>
+__global__ void __launch_bounds__(NTH, NC == 16 ? 2 : 1) k_full_tc(const __grid_constant__ KParams p,
                                                   const unsigned char *__restrict__ pack) {
-  using Lay = TcLayout<RM, PREC>;
+  using Lay = TcLayout<RM, PREC, NC>;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x;
   const int L = p.L;
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(NTH, 1) k_full_tc(const __grid_constant__ KPar
   float *red_s = fa + (L + 1) * RM;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((Lay::OFF_F + Lay::floats(L) * 4 + 15) & ~15));
   uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
-  if (tid < 32) tc::tmem_alloc(tbase, 512);
+  if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC>());
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
     tc::fence_mbar_init();
@@ -527,9 +529,9 @@ __global__ void __launch_bounds__(NTH, 1) k_full_tc(const __grid_constant__ KPar
     for (int j = tid; j < 4 * PL; j += NTH) red_s[j] = 0.0f;
     __syncthreads();
     if (T.kind == KIND_INT)
-      tc_tile<RM, PREC, 4>(p, T, tile, sm, pack, qst, tb, ctl, dead);
+      tc_tile<RM, PREC, 4, NC>(p, T, tile, sm, pack, qst, tb, ctl, dead);
     else
-      tc_tile<RM, PREC, 1>(p, T, tile, sm, pack, qst, tb, ctl, dead);
+      tc_tile<RM, PREC, 1, NC>(p, T, tile, sm, pack, qst, tb, ctl, dead);
     if (dead) break;
     if (p.grad) {
       __syncthreads();
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(NTH, 1) k_full_tc(const __grid_constant__ KPar
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid < 32) tc::tmem_dealloc(tb, 512);
+  if (tid < 32) tc::tmem_dealloc(tb, tmem_cols<NC>());
 }
 
 // host-side BF16 rounding (round to nearest even)
@@ -569,27 +571,35 @@ float bf16_val(uint16_t b) {
   return f;
 }
 
-template <int RM, int PREC>
+template <int RM, int PREC, int NC>
 cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaStream_t st) {
-  using Lay = TcLayout<RM, PREC>;
+  using Lay = TcLayout<RM, PREC, NC>;
   const size_t bytes = (size_t)Lay::bytes(p.L);
-  cudaError_t e = cudaFuncSetAttribute(k_full_tc<RM, PREC>,
+  cudaError_t e = cudaFuncSetAttribute(k_full_tc<RM, PREC, NC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(grid_cap, sms));
-  k_full_tc<RM, PREC><<<grid, NTH, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
+  // every CTA holds tmem_cols<NC>() TMEM columns: at most 512 / that many per SM
+  const int grid = std::max(1, std::min(grid_cap, sms * (512 / tmem_cols<NC>())));
+  k_full_tc<RM, PREC, NC><<<grid, NTH, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
   return cudaGetLastError();
 }
 
+template <int RM, int NC>
+int pk_chunk() { return Pk<RM, NC>::CHUNK; }
+
 }  // namespace
 
-int full_tc_supported(int L, int M, int RM) {
+int full_tc_supported(int L, int M, int RM, int NC) {
   if (RM != 16 && RM != 32) return 0;
+  if (NC != 16 && NC != 32) return 0;
   if (L < 1 || M < 1) return 0;
-  const int bytes = RM == 16 ? TcLayout<16, 3>::bytes(L) : TcLayout<32, 3>::bytes(L);
+  int bytes;
+  if (NC == 32) bytes = RM == 16 ? TcLayout<16, 3, 32>::bytes(L) : TcLayout<32, 3, 32>::bytes(L);
+  else bytes = RM == 16 ? TcLayout<16, 3, 16>::bytes(L) : TcLayout<32, 3, 16>::bytes(L);
+  // (16-column chunks run two CTAs per SM where their shared memory allows, else one)
   return bytes <= 227 * 1024 ? 1 : 0;
 }
 
@@ -599,25 +609,26 @@ size_t full_tc_scratch_floats(int L, int RM, int grid) {
   return (size_t)grid * (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * TNT;
 }
 
-size_t full_tc_pack_bytes(int L, int M, int RM) {
+size_t full_tc_pack_bytes(int L, int M, int RM, int NC) {
   const int NCH = (M + NC - 1) / NC;
-  const size_t chunk = RM == 16 ? Pk<16>::CHUNK : Pk<32>::CHUNK;
+  const size_t chunk = NC == 32 ? (RM == 16 ? pk_chunk<16, 32>() : pk_chunk<32, 32>())
+                                : (RM == 16 ? pk_chunk<16, 16>() : pk_chunk<32, 16>());
   return (size_t)L * NCH * chunk + 64;
 }
 
 // Pack the bases for the tensor-core kernel: per hidden layer l and chunk j of NC
-// rows, the K-major BF16 tiles of U^l (rows i, K = rank in), V^{l+1} (rows i,
+// (32 or 16) rows, the K-major BF16 tiles of U^l (rows i, K = rank in), V^{l+1} (rows i,
 // K = rank out), U^l^T and V^{l+1}^T (rows = rank, K = chunk) -- first their hi
 // pieces and the chunk's biases, then the mid pieces, then the lo pieces; ranks
 // are zero-padded to RM and rows to a multiple of NC.
-void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &U,
+void full_tc_pack(int L, int M, int RM, int NC, const std::vector<std::vector<double>> &U,
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
                   const int *r, std::vector<unsigned char> &out) {
   const int NCH = (M + NC - 1) / NC;
   const int T = NC * RM * 2;
   const int PIECE = 4 * T + 4 * NC;
   const int CHUNK = 3 * PIECE;
-  out.assign(full_tc_pack_bytes(L, M, RM), 0);
+  out.assign(full_tc_pack_bytes(L, M, RM, NC), 0);
   // three BF16 pieces: hi = rn(x), mid = rn(x - hi), lo = rn(x - hi - mid)
   auto put = [&](size_t base, int part, double x, int row, int k, int K) {
     const uint16_t h = bf16_bits((float)x);
@@ -661,13 +672,20 @@ void full_tc_pack(int L, int M, int RM, const std::vector<std::vector<double>> &
   std::memcpy(&out[(size_t)L * NCH * CHUNK], tail, sizeof(tail));
 }
 
-cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int grid_cap,
+cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int NC, int grid_cap,
                            cudaStream_t st) {
   const bool split = prec == LRNR_BF16X3;
-  if (p.RM == 16) return split ? launch_tc_t<16, 3>(p, tc_pack, grid_cap, st)
-                               : launch_tc_t<16, 1>(p, tc_pack, grid_cap, st);
-  if (p.RM == 32) return split ? launch_tc_t<32, 3>(p, tc_pack, grid_cap, st)
-                               : launch_tc_t<32, 1>(p, tc_pack, grid_cap, st);
+  if (NC == 32) {
+    if (p.RM == 16) return split ? launch_tc_t<16, 3, 32>(p, tc_pack, grid_cap, st)
+                                 : launch_tc_t<16, 1, 32>(p, tc_pack, grid_cap, st);
+    if (p.RM == 32) return split ? launch_tc_t<32, 3, 32>(p, tc_pack, grid_cap, st)
+                                 : launch_tc_t<32, 1, 32>(p, tc_pack, grid_cap, st);
+  } else if (NC == 16) {
+    if (p.RM == 16) return split ? launch_tc_t<16, 3, 16>(p, tc_pack, grid_cap, st)
+                                 : launch_tc_t<16, 1, 16>(p, tc_pack, grid_cap, st);
+    if (p.RM == 32) return split ? launch_tc_t<32, 3, 16>(p, tc_pack, grid_cap, st)
+                                 : launch_tc_t<32, 1, 16>(p, tc_pack, grid_cap, st);
+  }
   return cudaErrorInvalidValue;
 }
 

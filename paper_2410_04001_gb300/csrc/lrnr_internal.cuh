@@ -248,7 +248,9 @@ cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_
 // kernel is launched with exactly `grid` CTAs (its scratch is sized for them).
 cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st);
-cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int grid_cap,
+// NC: 32-column chunks (full-width networks, one CTA per SM) or 16-column chunks
+// (narrow networks, two CTAs per SM).
+cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int NC, int grid_cap,
                            cudaStream_t st);
 cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,
                           int rows_stride, float *loss_out, float *dL_ds, float *dL_db,
