@@ -320,7 +320,18 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
             errs.append(float(np.linalg.norm(ds - rs) / np.linalg.norm(rs)))
         r["err_dL_ds_sampled_instances"] = max(errs)
     out["batched_512_fast_fp32"] = r
-    del model, db, res
+    # the same batch through the reduced network on the tensor cores (BF16)
+    res16 = P.lrnr_residual_grad(model, "fast", "bf16", db)
+    P.lrnr_timing(model, True)
+    ts_, km, kn = timed_steps(lambda: P.lrnr_residual_grad(model, "fast", "bf16", db, out=res16), 10, model)
+    P.lrnr_timing(model, False)
+    ms = sum(ts_) / len(ts_)
+    ds32, ds16 = res[1].double(), res16[1].double()
+    out["batched_512_fast_bf16"] = {
+        "workload": r["workload"], "points": db.n_points, "points_per_s": db.n_points / (ms * 1e-3),
+        "ms_per_call": ms, "kernel_ms": km / max(1, kn),
+        "dL_ds_rel_diff_vs_fp32": float((ds16 - ds32).norm() / ds32.norm())}
+    del model, db, res, res16
     # 1,024 instances x 16,384 points, fused SPInProp steps
     net, bt = synth.workload_spinprop()
     model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
@@ -332,6 +343,13 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
     P.spinprop_step(model, "fast", "fp32", db, s, m, v, k, 2)
     ts_, _, _ = timed_steps(lambda: P.spinprop_step(model, "fast", "fp32", db, s, m, v, k, 1), 10)
     ms = sum(ts_) / len(ts_)
+    s16, m16, v16 = db.s.clone(), torch.zeros_like(s), torch.zeros_like(s)
+    k16 = torch.zeros(1, dtype=torch.int64, device=dev)
+    P.spinprop_step(model, "fast", "bf16", db, s16, m16, v16, k16, 2)
+    ts16, _, _ = timed_steps(lambda: P.spinprop_step(model, "fast", "bf16", db, s16, m16, v16, k16, 1), 10)
+    ms16 = sum(ts16) / len(ts16)
+    out["spinprop_1024_fast_bf16"] = {"points": db.n_points, "steps_per_s": 1e3 / ms16,
+                                      "points_per_s": db.n_points / (ms16 * 1e-3), "ms_per_step": ms16}
     out["spinprop_1024_fast_fp32"] = {
         "workload": "1,024 CDR instances x 16,384 points, M=512 r=16 L=5 rhat=16, one Adam step",
         "points": db.n_points, "steps_per_s": 1e3 / ms, "points_per_s": db.n_points / (ms * 1e-3),
@@ -361,17 +379,18 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
     out["spinprop_fast_vs_full_16_instances"] = cmp
     del model, db, dsub
     out["paper_d1_fast_phase"] = paper_fast_phase(P, synth, np, torch, dev)
+    out["paper_d2_fast_phase_bf16"] = paper_fast_phase(P, synth, np, torch, dev, d2=True)
     return out
 
 
-def paper_fast_phase(P, synth, np, torch, dev):
+def paper_fast_phase(P, synth, np, torch, dev, d2=False):
     """The fast phase on the paper's convection architecture in shape (M = 4,000,
     r = (1, 5, 5, 3, 1), rhat = 5, X = 12 points, l1 loss + locality, Adam), against a
     full-width fine-tune Adam step (MSE over 69,632 collocation points), both FP32
     and graph-captured; the paper quotes 0.004 s vs 0.14 s per step on a V100 for its
     rank-49 architecture (context only)."""
     from paper_2410_04001_gb300 import fastphase
-    net, bx, bt = synth.workload_paper_d1()
+    net, bx, bt = synth.workload_paper_d2() if d2 else synth.workload_paper_d1()
     model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
     g = synth.rng(77)
     xs, ts = synth.snapshot_design(g, 8)
@@ -386,9 +405,12 @@ def paper_fast_phase(P, synth, np, torch, dev):
     build_ms = e0.elapsed_time(e1)
     dX = P.DeviceBatch.from_host(bx, dev)
     dT = P.DeviceBatch.from_host(bt, dev)
-    res = {"workload": "M=4000, r=(1,5,5,3,1), convection beta=7; fast phase on the 12-point "
-                       "4x3 grid (l1 + locality 1e-3, lr 1e-3); fine-tune on 65,536 + 2,048 + "
-                       "1,024 pairs (MSE)", "build_reduced_ms": build_ms}
+    res = {"workload": ("M=4000, r=(1,49,30,25,1), CDR mu=(2,1,1), BF16 on the tensor cores "
+                        "(rank 49 is beyond the FP32 kernels)" if d2 else
+                        "M=4000, r=(1,5,5,3,1), convection beta=7") +
+                       "; fast phase on the 12-point 4x3 grid (l1 + locality 1e-3, lr 1e-3); "
+                       "fine-tune on 65,536 + 2,048 + 1,024 pairs (MSE)", "build_reduced_ms": build_ms}
+    fprec = "bf16" if d2 else "fp32"
 
     def step_time(form, batch, loss, lam, reps=200, prec="fp32"):
         s = batch.s.clone()
@@ -413,22 +435,22 @@ def paper_fast_phase(P, synth, np, torch, dev):
         torch.cuda.synchronize()
         return a.elapsed_time(b) * 1e3 / reps
 
-    fast_us = step_time("fast", dX, "l1", 1e-3)
-    full_us = step_time("full", dT, "mse", 0.0, reps=20)
+    fast_us = step_time("fast", dX, "l1", 1e-3, prec=fprec)
     try:
-        full_bf16_us = step_time("full", dT, "mse", 0.0, reps=20, prec="bf16")
+        full_us = step_time("full", dT, "mse", 0.0, reps=20)
     except P.LrnrError as e:
-        full_bf16_us = str(e)
+        full_us = str(e)
+    full_bf16_us = step_time("full", dT, "mse", 0.0, reps=20, prec="bf16")
     # the whole fast phase: 400 Adam steps (the paper's epoch budget) in one call
     e0.record()
-    s_fast = fastphase.fast_phase(model, dX, 400, lr=1e-3, lambda_loc=1e-3)
+    s_fast = fastphase.fast_phase(model, dX, 400, lr=1e-3, lambda_loc=1e-3, prec=fprec)
     e1.record()
     torch.cuda.synchronize()
-    lf0, _, _ = P.lrnr_residual_grad(model, "full", "fp32", dT, want_db=False)
-    lf1, _, _ = P.lrnr_residual_grad(model, "full", "fp32", dT.with_s(s_fast), want_db=False)
-    res.update({"fast_step_us": fast_us, "full_finetune_step_us": full_us,
+    lf0, _, _ = P.lrnr_residual_grad(model, "full", fprec, dT, want_db=False)
+    lf1, _, _ = P.lrnr_residual_grad(model, "full", fprec, dT.with_s(s_fast), want_db=False)
+    res.update({"fast_step_us": fast_us, "fast_prec": fprec, "full_finetune_step_us": full_us,
                 "full_finetune_step_bf16_us": full_bf16_us,
-                "full_over_fast_step_ratio": full_us / fast_us,
+                "full_bf16_over_fast_step_ratio": full_bf16_us / fast_us,
                 "fast_phase_400_steps_ms": e0.elapsed_time(e1),
                 "finetune_loss_at_s0": float(lf0[0]), "finetune_loss_at_s_fast": float(lf1[0]),
                 "s_fast_minus_s0_max": float((s_fast - dX.s).abs().max())})

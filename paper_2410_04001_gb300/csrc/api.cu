@@ -18,7 +18,7 @@ cudaError_t launch_snapshots_f64(const double *w64, int L, int M, const int *r_d
                                  const int64_t *offs_dev, int layer, int64_t n_pts,
                                  const double *x, const double *t, int n_s, const double *s,
                                  int sum_r, double *out, cudaStream_t st);
-int full_tc_supported(int L, int M, int RM, int NC);
+int full_tc_supported(int L, int M, int RM, int NC, int split);
 size_t full_tc_pack_bytes(int L, int M, int RM, int NC);
 void full_tc_pack(int L, int M, int RM, int NC, const std::vector<std::vector<double>> &U,
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
@@ -44,6 +44,7 @@ struct lrnr_model {
   int64_t *offs_dev = nullptr;
   void *tc_pack = nullptr;                     // tensor-core operand pack (full form)
   void *ftc_pack = nullptr;                    // tensor-core pack of the reduced network
+  int ftc_nc = 16;                             // its chunk width (32 at rank 64)
   // reduced layers (host, FP64): Uh [rh][r_l], bh [rh], Vh [rh][r_{l+1}], rows [rh]
   int rhat[LMAX] = {0};
   std::vector<std::vector<double>> Uh, bh, Vh;
@@ -85,7 +86,7 @@ lrnr_status cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
-int pad_rank(int r) { return r <= 8 ? 8 : (r <= 16 ? 16 : 32); }
+int pad_rank(int r) { return r <= 8 ? 8 : (r <= 16 ? 16 : (r <= 32 ? 32 : 64)); }
 
 struct DeviceGuard {
   int prev = -1;
@@ -204,7 +205,8 @@ lrnr_status build_fast_pack(lrnr_model *m) {
   if (m->ftc_pack) cudaFree(m->ftc_pack);
   m->ftc_pack = nullptr;
   const int RMt = std::max(16, RMp);
-  if (full_tc_supported(L, RHp, RMt, 16)) {
+  m->ftc_nc = RMt <= 32 ? 16 : 32;
+  if (full_tc_supported(L, RHp, RMt, m->ftc_nc, 0)) {
     std::vector<std::vector<double>> Ur(L + 1), Vr(L + 1), br(L + 1);
     Vr[0] = m->V[0];
     Ur[L] = m->U[L];
@@ -221,7 +223,7 @@ lrnr_status build_fast_pack(lrnr_model *m) {
       }
     }
     std::vector<unsigned char> tp;
-    full_tc_pack(L, RHp, RMt, 16, Ur, Vr, br, m->r, tp);
+    full_tc_pack(L, RHp, RMt, m->ftc_nc, Ur, Vr, br, m->r, tp);
     CK(cudaMalloc(&m->ftc_pack, tp.size()));
     CK(cudaMemcpy(m->ftc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice));
   }
@@ -270,7 +272,9 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     // the reduced network on the tensor cores: an LRNR of width RH
     rc = build_fast_pack(m);
     if (rc != LRNR_OK) return rc;
-    if (!m->ftc_pack) return LRNR_ENOTSUP;
+    if (!m->ftc_pack || !full_tc_supported(m->L, m->fRH, std::max(16, m->fRM), m->ftc_nc,
+                                           prec == LRNR_BF16X3))
+      return LRNR_ENOTSUP;
     p.RM = std::max(16, m->fRM);
     p.RH = m->fRH;
     p.M = m->fRH;
@@ -301,6 +305,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     p.RM = m->RM;
     p.RH = 0;
     if (prec == LRNR_FP32) {
+      if (p.RM > 32) return LRNR_ENOTSUP;   // the FP32 full-width kernel holds rank <= 32 jets
       p.pack = m->full_pack;
       p.nt = full_fp32_choose_nt(m->L, p.RM, partial_len(m->L, p.RM, m->L * m->M + 1));
       if (!p.nt) return LRNR_ENOTSUP;
@@ -311,7 +316,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
         p.nt = tn;
     } else if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
       p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
-      if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM, 32)) return LRNR_ENOTSUP;
+      if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM, 32, prec == LRNR_BF16X3))
+        return LRNR_ENOTSUP;
       p.pack = nullptr;
       p.nt = full_tc_nt();
     } else {
@@ -329,7 +335,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   size_t scr_bytes = 0;
   if (tc) {
     // one CTA per SM with 32-column chunks, two with 16-column chunks (reduced form)
-    ps.grid_cap = (int)std::min<int64_t>(tiles, (form == LRNR_FAST ? 2 : 1) * (int64_t)m->num_sms);
+    const int per_sm = (form == LRNR_FAST && m->ftc_nc == 16) ? 2 : 1;
+    ps.grid_cap = (int)std::min<int64_t>(tiles, per_sm * (int64_t)m->num_sms);
     scr_bytes = full_tc_scratch_floats(m->L, p.RM, ps.grid_cap) * sizeof(float);
   } else if (form == LRNR_FAST) {
     // the FastLRNR kernel keeps layer inputs in a per-CTA scratch: size the grid first
@@ -418,7 +425,8 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
   }
   if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
     const bool fast = form == LRNR_FAST;
-    CK(launch_full_tc(p, fast ? m->ftc_pack : m->tc_pack, (int)prec, fast ? 16 : 32, ps.grid_cap, st));
+    CK(launch_full_tc(p, fast ? m->ftc_pack : m->tc_pack, (int)prec, fast ? m->ftc_nc : 32,
+                      ps.grid_cap, st));
   } else if (form == LRNR_FAST) {
     CK(launch_fast(p, ps.grid_cap, st));
   } else {
@@ -537,7 +545,7 @@ lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U, const
   if ((e = cudaMemcpy(m->offs_dev, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&m->status_dev, sizeof(int))) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(m->status_dev, 0, sizeof(int))) != cudaSuccess) return fail(e);
-  if (full_tc_supported(L, M, std::max(16, RM), 32)) {
+  if (full_tc_supported(L, M, std::max(16, RM), 32, 0)) {
     std::vector<unsigned char> tp;
     full_tc_pack(L, M, std::max(16, RM), 32, m->U, m->V, m->b, m->r, tp);
     if ((e = cudaMalloc(&m->tc_pack, tp.size())) != cudaSuccess) return fail(e);
@@ -814,15 +822,16 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   const int nt_min = 32;
   const int64_t tiles = max_points / nt_min + 3 * (int64_t)max_inst + 3;
   int Pmax = partial_len(m->L, m->RM, m->L * m->M + 1);
-  Pmax = std::max(Pmax, partial_len(m->L, RMAX, m->L * RHMAX + 1));
+  const int RMm = std::max(16, m->RM);   // largest padded rank any path uses for this model
+  Pmax = std::max(Pmax, partial_len(m->L, RMm, m->L * RHMAX + 1));
   // per-CTA layer-input stores (tensor-core and FastLRNR kernels): at most 4 CTAs per SM
-  const size_t store = std::max(std::max(full_tc_scratch_floats(m->L, RMAX, 2 * m->num_sms),
-                                         fast_scratch_floats(m->L, RMAX, RHMAX, 128, 4 * m->num_sms)),
-                                full_fp32_scratch_floats(m->L, RMAX, 64, 8 * m->num_sms));
+  const size_t store = std::max(std::max(full_tc_scratch_floats(m->L, RMm, 2 * m->num_sms),
+                                         fast_scratch_floats(m->L, RMm, RHMAX, 128, 4 * m->num_sms)),
+                                full_fp32_scratch_floats(m->L, RMm, 64, 8 * m->num_sms));
   const size_t need = align256(sizeof(int32_t) * (size_t)(max_inst + 1)) +
                       align256((size_t)tiles * Pmax * sizeof(float)) +
                       align256(store * sizeof(float)) +
-                      align256(adam_group_floats(max_inst, m->L, RMAX) * sizeof(float)) +
+                      align256(adam_group_floats(max_inst, m->L, RMm) * sizeof(float)) +
                       align256((size_t)(tiles / kRedGroup + 1 + max_inst) * Pmax * sizeof(float));
   lrnr_status rc = ensure_tickets(m, tiles / kRedGroup + 2 + 2 * (int64_t)max_inst, nullptr);
   if (rc != LRNR_OK) return rc;

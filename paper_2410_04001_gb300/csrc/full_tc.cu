@@ -42,9 +42,10 @@ constexpr int TNT = 128;   // points per tile = TMEM lanes
 constexpr int NTH = 256;   // threads: two per point (column halves of a chunk)
 // NC: hidden-width chunk, 32 (full-width networks: one CTA and 512 TMEM columns per
 // SM) or 16 (narrow networks such as the FastLRNR reduced layers: two CTAs and 256
-// TMEM columns each per SM, so that one CTA's epilogue overlaps the other's MMAs).
-template <int NC>
-constexpr int tmem_cols() { return NC == 16 ? 256 : 512; }
+// TMEM columns each per SM, so that one CTA's epilogue overlaps the other's MMAs; with
+// rank 64 the rank-r accumulators alone take 256 columns and one CTA runs per SM).
+template <int NC, int RM>
+constexpr int tmem_cols() { return (NC == 16 && RM <= 32) ? 256 : 512; }
 
 // Chunk block of the packed bases (bytes), three equal groups of PIECE bytes: the
 // hi pieces of Ub (NC x RM), Vb (NC x RM), Utb (RM x NC), Vtb (RM x NC) followed by
@@ -493,7 +494,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 }
 
 template <int RM, int PREC, int NC>
-__global__ void __launch_bounds__(NTH, NC == 16 ? 2 : 1) k_full_tc(const __grid_constant__ KParams p,
+__global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_full_tc(const __grid_constant__ KParams p,
                                                   const unsigned char *__restrict__ pack) {
   using Lay = TcLayout<RM, PREC, NC>;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(NTH, NC == 16 ? 2 : 1) k_full_tc(const __grid_
   float *red_s = fa + (L + 1) * RM;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((Lay::OFF_F + Lay::floats(L) * 4 + 15) & ~15));
   uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
-  if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC>());
+  if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC, RM>());
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
     tc::fence_mbar_init();
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(NTH, NC == 16 ? 2 : 1) k_full_tc(const __grid_
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid < 32) tc::tmem_dealloc(tb, tmem_cols<NC>());
+  if (tid < 32) tc::tmem_dealloc(tb, tmem_cols<NC, RM>());
 }
 
 // host-side BF16 rounding (round to nearest even)
@@ -581,8 +582,8 @@ cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaSt
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // every CTA holds tmem_cols<NC>() TMEM columns: at most 512 / that many per SM
-  const int grid = std::max(1, std::min(grid_cap, sms * (512 / tmem_cols<NC>())));
+  // every CTA holds tmem_cols<NC, RM>() TMEM columns: at most 512 / that many per SM
+  const int grid = std::max(1, std::min(grid_cap, sms * (512 / tmem_cols<NC, RM>())));
   k_full_tc<RM, PREC, NC><<<grid, NTH, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
   return cudaGetLastError();
 }
@@ -592,13 +593,17 @@ int pk_chunk() { return Pk<RM, NC>::CHUNK; }
 
 }  // namespace
 
-int full_tc_supported(int L, int M, int RM, int NC) {
-  if (RM != 16 && RM != 32) return 0;
+int full_tc_supported(int L, int M, int RM, int NC, int split) {
+  if (RM != 16 && RM != 32 && RM != 64) return 0;
   if (NC != 16 && NC != 32) return 0;
   if (L < 1 || M < 1) return 0;
+  if (RM == 64 && (split || NC == 16)) return 0;   // rank 64: BF16, 32-column chunks only
   int bytes;
-  if (NC == 32) bytes = RM == 16 ? TcLayout<16, 3, 32>::bytes(L) : TcLayout<32, 3, 32>::bytes(L);
-  else bytes = RM == 16 ? TcLayout<16, 3, 16>::bytes(L) : TcLayout<32, 3, 16>::bytes(L);
+  if (RM == 64) bytes = TcLayout<64, 1, 32>::bytes(L);
+  else if (NC == 32 && split) bytes = RM == 16 ? TcLayout<16, 3, 32>::bytes(L) : TcLayout<32, 3, 32>::bytes(L);
+  else if (NC == 32) bytes = RM == 16 ? TcLayout<16, 1, 32>::bytes(L) : TcLayout<32, 1, 32>::bytes(L);
+  else if (split) bytes = RM == 16 ? TcLayout<16, 3, 16>::bytes(L) : TcLayout<32, 3, 16>::bytes(L);
+  else bytes = RM == 16 ? TcLayout<16, 1, 16>::bytes(L) : TcLayout<32, 1, 16>::bytes(L);
   // (16-column chunks run two CTAs per SM where their shared memory allows, else one)
   return bytes <= 227 * 1024 ? 1 : 0;
 }
@@ -611,8 +616,9 @@ size_t full_tc_scratch_floats(int L, int RM, int grid) {
 
 size_t full_tc_pack_bytes(int L, int M, int RM, int NC) {
   const int NCH = (M + NC - 1) / NC;
-  const size_t chunk = NC == 32 ? (RM == 16 ? pk_chunk<16, 32>() : pk_chunk<32, 32>())
-                                : (RM == 16 ? pk_chunk<16, 16>() : pk_chunk<32, 16>());
+  const size_t chunk =
+      NC == 32 ? (RM == 16 ? pk_chunk<16, 32>() : (RM == 32 ? pk_chunk<32, 32>() : pk_chunk<64, 32>()))
+               : (RM == 16 ? pk_chunk<16, 16>() : (RM == 32 ? pk_chunk<32, 16>() : pk_chunk<64, 16>()));
   return (size_t)L * NCH * chunk + 64;
 }
 
@@ -680,6 +686,7 @@ cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int 
                                  : launch_tc_t<16, 1, 32>(p, tc_pack, grid_cap, st);
     if (p.RM == 32) return split ? launch_tc_t<32, 3, 32>(p, tc_pack, grid_cap, st)
                                  : launch_tc_t<32, 1, 32>(p, tc_pack, grid_cap, st);
+    if (p.RM == 64 && !split) return launch_tc_t<64, 1, 32>(p, tc_pack, grid_cap, st);
   } else if (NC == 16) {
     if (p.RM == 16) return split ? launch_tc_t<16, 3, 16>(p, tc_pack, grid_cap, st)
                                  : launch_tc_t<16, 1, 16>(p, tc_pack, grid_cap, st);

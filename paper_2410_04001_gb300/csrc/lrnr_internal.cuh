@@ -17,7 +17,7 @@ namespace lrnr {
 
 constexpr int LMAX = 16;      // hidden layers supported
 constexpr int R1 = 2;         // padded rank of the input layer (input is (x, t))
-constexpr int RMAX = 32;      // largest hidden rank
+constexpr int RMAX = 64;      // largest padded hidden rank
 constexpr int RHMAX = 32;     // largest EIM row count per layer
 constexpr float TWO_PI_F = 6.28318530717958647692f;
 
@@ -249,7 +249,7 @@ cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_
 cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st);
 // NC: 32-column chunks (full-width networks, one CTA per SM) or 16-column chunks
-// (narrow networks, two CTAs per SM).
+// (narrow networks, two CTAs per SM while RM <= 32).
 cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int NC, int grid_cap,
                            cudaStream_t st);
 cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,

@@ -30,24 +30,28 @@ def build_reduced(model: B.Model, x, t, s_draws, rhat: int, tol: float = 0.0, st
 
 
 def fast_phase(model: B.Model, batch_X: B.DeviceBatch, n_steps: int, lr: float = 1e-3,
-               lambda_loc: float = 0.0, s_anchor=None, loss_out=None, stream=None):
+               lambda_loc: float = 0.0, s_anchor=None, loss_out=None, prec: str = "fp32",
+               stream=None):
     """``n_steps`` Adam steps on the coefficients of ``batch_X`` (its ``s`` is copied,
     not modified) minimising the fast loss of Eq. 3.6 plus lambda_loc times the
     locality term of Eq. 3.7 (anchor ``s_anchor``, the coefficients the phase starts
-    from when omitted).  Returns the trained coefficients s_fast (device, FP32)."""
+    from when omitted).  ``prec``: "fp32" (FP32 kernel) or "bf16" / "bf16x3" (the
+    reduced network on the tensor cores).  Returns the trained coefficients s_fast
+    (device, FP32)."""
     s = batch_X.s.clone()
     anchor = s.clone() if s_anchor is None else s_anchor
     m = torch.zeros_like(s)
     v = torch.zeros_like(s)
     step = torch.zeros(1, dtype=torch.int64, device=s.device)
-    B.spinprop_step(model, "fast", "fp32", batch_X, s, m, v, step, n_steps=n_steps, lr=lr,
+    B.spinprop_step(model, "fast", prec, batch_X, s, m, v, step, n_steps=n_steps, lr=lr,
                     lambda_loc=lambda_loc, s_anchor=anchor, loss="l1", loss_out=loss_out,
                     stream=stream)
     return s
 
 
-def fast_solution(model: B.Model, batch_eval: B.DeviceBatch, s_fast, stream=None):
+def fast_solution(model: B.Model, batch_eval: B.DeviceBatch, s_fast, prec: str = "fp32",
+                  stream=None):
     """u_FASTSOL at the interior points of ``batch_eval``: the full-width LRNR with the
     coefficients s_fast (returns u and the CDR residual at those points)."""
-    out = B.lrnr_residual(model, "full", "fp32", batch_eval.with_s(s_fast), stream=stream)
+    out = B.lrnr_residual(model, "full", prec, batch_eval.with_s(s_fast), stream=stream)
     return out

@@ -211,23 +211,35 @@ def workload_spinprop(n_inst: int = 1024, per_inst: int = 16384):
     return net, bt
 
 
+def _paper_workload(seed: int, M: int, rk, mu, n_tune: int):
+    g = rng(seed)
+    net = make_net_ranks(g, M, rk)
+    s = make_s(g, 1, net.sum_r)
+    gx = TWO_PI * (np.arange(4) + 0.5) / 4.0
+    gt = (np.arange(3) + 0.5) / 3.0
+    X, T = np.meshgrid(gx, gt, indexing="ij")
+    beta, nu, rho = mu
+    bx = Batch(beta=np.array([beta]), nu=np.array([nu]), rho=np.array([rho]), s=s.copy(),
+               int_off=_offsets([12]), ic_off=_offsets([0]), bc_off=_offsets([0]),
+               x_int=X.ravel(), t_int=T.ravel(), x_ic=np.zeros(0), t_bc=np.zeros(0))
+    bt = make_batch(g, net, n_tune, n_tune // 32, n_tune // 64, beta, nu, rho, s=s.copy())
+    return net, bx, bt
+
+
 def workload_paper_d1(M: int = 4000, n_tune: int = 65536, beta: float = 7.0):
     """The paper's convection setting in shape: LRNR of width M = 4,000 with ranks
     r = (1, 5, 5, 3, 1) (four hidden layers), pure convection with beta = 7; the fast
     phase samples X = the 4 x 3 cell-centred grid (12 interior points) and the
     fine-tune phase the collocation batch (n_tune interior, n_tune/32 initial,
     n_tune/64 periodic pairs).  Returns (net, batch_X, batch_tune)."""
-    g = rng(1005)
-    net = make_net_ranks(g, M, [1, 5, 5, 3, 1])
-    s = make_s(g, 1, net.sum_r)
-    gx = TWO_PI * (np.arange(4) + 0.5) / 4.0
-    gt = (np.arange(3) + 0.5) / 3.0
-    X, T = np.meshgrid(gx, gt, indexing="ij")
-    bx = Batch(beta=np.array([beta]), nu=np.zeros(1), rho=np.zeros(1), s=s.copy(),
-               int_off=_offsets([12]), ic_off=_offsets([0]), bc_off=_offsets([0]),
-               x_int=X.ravel(), t_int=T.ravel(), x_ic=np.zeros(0), t_bc=np.zeros(0))
-    bt = make_batch(g, net, n_tune, n_tune // 32, n_tune // 64, beta, 0.0, 0.0, s=s.copy())
-    return net, bx, bt
+    return _paper_workload(1005, M, [1, 5, 5, 3, 1], (beta, 0.0, 0.0), n_tune)
+
+
+def workload_paper_d2(M: int = 4000, n_tune: int = 65536, mu=(2.0, 1.0, 1.0)):
+    """The paper's convection-diffusion-reaction setting in shape: width M = 4,000,
+    ranks r = (1, 49, 30, 25, 1), mu = (2, 1, 1) inside its parameter box
+    [(1, 0, 0), (3, 2, 2)]; sample sets as in ``workload_paper_d1``."""
+    return _paper_workload(1006, M, [1, 49, 30, 25, 1], mu, n_tune)
 
 
 def snapshot_design(g: np.random.Generator, n_per_point: int = 8, std: float = 0.05):
