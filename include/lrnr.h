@@ -15,7 +15,10 @@
  *   r[l]   rank of weight layer l, W^l = U^l diag(s^l) V^l^T (Sec. 2.1 Eq. 2.2).
  *          U^l is M_l x r[l], V^l is M_{l-1} x r[l] (V has as many rows as the
  *          layer's input; the printed M_l rows cannot multiply z^{l-1}).
- *          Constraints: 1 <= r[0] <= 2, 1 <= r[l] <= 32 for 0 < l < L, r[L] == 1.
+ *          Constraints: 1 <= r[0] <= 2, 1 <= r[l] <= 64 for 0 < l < L, r[L] == 1.
+ *          Ranks are padded to 8, 16, 32 or 64.  The FP32 kernels take padded ranks
+ *          up to 32 (FastLRNR FP32: 16); rank 64 runs in LRNR_BF16 on the tensor
+ *          cores only; other combinations return LRNR_ENOTSUP.
  *   s      coefficients, per PDE instance a vector of sum(r) floats, layer-major.
  *   b      biases, b^l of length M_l; sum over layers = L*M + 1 ("sum_m").
  *   mu     (beta, nu, rho): N[u] = u_t + beta u_x - nu u_xx - rho u (1-u)
@@ -64,8 +67,10 @@ typedef enum {
 typedef enum {
   LRNR_FP32 = 0,        /* FP32 SIMT everywhere (reference precision of the GPU path) */
   LRNR_TF32 = 1,        /* reserved */
-  LRNR_BF16 = 2,        /* full form: tcgen05 BF16 operands, FP32 accumulation in TMEM */
-  LRNR_BF16X3 = 3       /* full form: split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+  LRNR_BF16 = 2,        /* tcgen05 BF16 operands, FP32 accumulation in TMEM (both forms;
+                           the reduced network is an LRNR of width rhat, Sec. 2.2 Eq. 2.8) */
+  LRNR_BF16X3 = 3       /* split-BF16: activations hi + lo, bases hi + mid + lo, products
+                           hi*hi + hi*mid + lo*hi + hi*lo + lo*mid, FP32 accumulation */
 } lrnr_precision;
 
 typedef enum { LRNR_FULL = 0, LRNR_FAST = 1 } lrnr_form;
