@@ -517,15 +517,25 @@ def main():
     def spin():
         P.spinprop_step(model, "fast", "fp32", db, s, m, v, step_ctr, 1, lr=1e-3, loss_out=loss_out)
 
-    # CUDA graph of one step (3 kernels); kernel timing events are recorded inside it
-    P.lrnr_timing(model, True)
+    # CUDA graph of one step (2 kernels).  Kernel timing: every 8th timed step runs the
+    # same step eagerly with the library's timing events around the FastLRNR kernel;
+    # all events are read once, after the timed region, so that the host never waits
+    # for the GPU inside it (the host enqueues ahead and the GPU never idles).
     for _ in range(3):
         spin()
     torch.cuda.synchronize()
-    P.lrnr_timing_read(model)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, capture_error_mode="relaxed"):
         spin()
+    step_counter = [0]
+
+    def replay():
+        step_counter[0] += 1
+        if step_counter[0] % 8 == 1:
+            spin()
+        else:
+            graph.replay()
+
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def timed_steps(fn, n, timing_model=None):
@@ -547,9 +557,9 @@ def main():
         return [a.elapsed_time(b) for a, b in ev], kern, kl
 
     for _ in range(args.warmup):
-        graph.replay()
-        P.lrnr_timing_read(model)
+        replay()
     torch.cuda.synchronize()
+    P.lrnr_timing(model, True)
     P.lrnr_timing_read(model)
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -561,9 +571,11 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    per_step, kern_ms, kern_n = timed_steps(graph.replay, args.steps, model)
+    per_step, _, _ = timed_steps(replay, args.steps)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    kern_ms, kern_n = P.lrnr_timing_read(model)
+    P.lrnr_timing(model, False)
     if dist:
         dist.barrier()
     clk = clocks.stop()

@@ -191,14 +191,20 @@ __global__ void __launch_bounds__(256) k_reduce_adam2(const __grid_constant__ Ad
   const int DB0 = 1 + (a.L + 1) * a.RM;
   float *grow = gsum + ((int64_t)i * kAdamGroups + g) * DB0;
   for (int j = tid; j < DB0; j += 256) {
-    float a0 = 0.0f, a1 = 0.0f;
-    int t = t0 + g;
-    for (; t + kAdamGroups < t1; t += 2 * kAdamGroups) {
-      a0 += __ldg(a.partial + (int64_t)t * a.P + j);
-      a1 += __ldg(a.partial + (int64_t)(t + kAdamGroups) * a.P + j);
+    // rows t0 + g, t0 + g + G, ... in order; the loads of up to 16 rows are issued
+    // before their additions (one L2 round trip per 16 rows)
+    float acc = 0.0f;
+    for (int t = t0 + g; t < t1; t += 16 * kAdamGroups) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int tq = t + q * kAdamGroups;
+        v[q] = tq < t1 ? __ldg(a.partial + (int64_t)tq * a.P + j) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc += v[q];
     }
-    if (t < t1) a0 += __ldg(a.partial + (int64_t)t * a.P + j);
-    grow[j] = a0 + a1;
+    grow[j] = acc;
   }
   __threadfence();
   __syncthreads();
@@ -208,8 +214,12 @@ __global__ void __launch_bounds__(256) k_reduce_adam2(const __grid_constant__ Ad
   __threadfence();
   const float *gi = gsum + (int64_t)i * kAdamGroups * DB0;
   for (int j = tid; j < DB0; j += 256) {
+    float v[kAdamGroups];
+#pragma unroll
+    for (int gg = 0; gg < kAdamGroups; ++gg) v[gg] = __ldcg(gi + gg * DB0 + j);
     float tot = 0.0f;
-    for (int gg = 0; gg < kAdamGroups; ++gg) tot += __ldcg(gi + gg * DB0 + j);
+#pragma unroll
+    for (int gg = 0; gg < kAdamGroups; ++gg) tot += v[gg];
     if (j == 0) loss_sh = tot;
     else {
       const int l = (j - 1) / a.RM, k = (j - 1) % a.RM;
