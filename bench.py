@@ -594,8 +594,13 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_max)
     achieved = flops_launch / (k_avg_ms * 1e-3) / 1e12
+    try:
+        mp = P.lrnr_measure_peaks()
+    except P.LrnrError as e:
+        mp = {"unavailable": str(e)}
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": K_FAST_DRAM_BYTES,
+            "microbench": mp,
             "kernel": "k_fast<16,16> (fused FastLRNR residual + adjoint)",
             "kernel_ms": k_avg_ms, "flops_per_launch": flops_launch,
             "peak_note": f"FP32 FMA peak = 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (max SM clock, {src} peaks file)"}

@@ -251,6 +251,20 @@ lrnr_status lrnr_timing(lrnr_model *m, int enable);
  * read.  lrnr_timing releases them. */
 lrnr_status lrnr_timing_read(lrnr_model *m, double *ms_total, int64_t *launches);
 
+/* lrnr_measure_peaks -- compute-throughput microbenchmarks of the current device
+ * (the roofline denominators of the FP32 SIMT kernels; the paper has no counterpart):
+ * FP32 fused multiply-add, scalar and packed two-lane (TFLOP/s, 2 flops per lane
+ * FMA), tanh.approx.f32 and tanhf (10^9 results/s), FP64 FMA (TFLOP/s), and the SM
+ * clock while they ran (MHz, from clock64 over CUDA-event time).  Runs on `stream`
+ * (a few tens of ms), allocates and frees a few KB of device memory, synchronises.
+ * Errors: LRNR_EINVAL (out NULL), LRNR_ENOMEM, LRNR_ECUDA. */
+typedef struct {
+  double fp32_fma_tflops, fp32_fma2_tflops, tanh_approx_gops, tanhf_gops, fp64_fma_tflops;
+  double sm_mhz;
+  int sms;
+} lrnr_peaks;
+lrnr_status lrnr_measure_peaks(lrnr_peaks *out, void *stream);
+
 /* lrnr_last_device_status -- synchronises the device, returns and clears the
  * status word written by kernels (LRNR_OK if none). */
 lrnr_status lrnr_last_device_status(lrnr_model *m);

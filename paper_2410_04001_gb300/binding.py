@@ -67,6 +67,7 @@ _SIGS = {
     "lrnr_last_device_status": (ctypes.c_int, [_P]),
     "lrnr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lrnr_destroy": (None, [_P]),
+    "lrnr_measure_peaks": (ctypes.c_int, [_P, _P]),
 }
 
 EXPORTS = tuple(_SIGS)
@@ -182,6 +183,20 @@ def lrnr_timing_read(model: Model):
     n = ctypes.c_int64(0)
     _check(lib().lrnr_timing_read(model.handle, ctypes.byref(ms), ctypes.byref(n)), "lrnr_timing_read")
     return ms.value, n.value
+
+
+class lrnr_peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_tflops", ctypes.c_double), ("fp32_fma2_tflops", ctypes.c_double),
+                ("tanh_approx_gops", ctypes.c_double), ("tanhf_gops", ctypes.c_double),
+                ("fp64_fma_tflops", ctypes.c_double), ("sm_mhz", ctypes.c_double),
+                ("sms", ctypes.c_int)]
+
+
+def lrnr_measure_peaks(stream=None) -> dict:
+    """Compute-throughput microbenchmarks of the current device (see include/lrnr.h)."""
+    out = lrnr_peaks()
+    _check(lib().lrnr_measure_peaks(ctypes.byref(out), _stream(stream)), "lrnr_measure_peaks")
+    return {name: getattr(out, name) for name, _ in lrnr_peaks._fields_}
 
 
 def lrnr_last_device_status(model: Model) -> int:

@@ -121,3 +121,13 @@ def test_unsupported_combinations_are_reported(P):
     with pytest.raises(P.LrnrError) as e:
         P.lrnr_residual_grad(model, "full", "tf32", db)
     assert e.value.status == P.binding.ENOTSUP
+
+
+def test_peak_microbenchmarks_are_plausible(P):
+    """The FP32 FMA microbenchmark reaches the unit-count peak (152 SMs x 128 lanes x 2
+    flops x clock) within a few percent; the others report positive rates."""
+    pk = P.lrnr_measure_peaks()
+    formula = pk["sms"] * 128 * 2 * pk["sm_mhz"] * 1e6 / 1e12
+    assert 0.8 * formula < max(pk["fp32_fma_tflops"], pk["fp32_fma2_tflops"]) < 1.1 * formula, (pk, formula)
+    assert pk["tanh_approx_gops"] > 0 and pk["tanhf_gops"] > 0 and pk["fp64_fma_tflops"] > 0
+    assert 500 < pk["sm_mhz"] < 2500
