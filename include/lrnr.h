@@ -233,6 +233,16 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst);
 lrnr_status lrnr_set_tuning(lrnr_model *m, lrnr_form form, lrnr_precision prec, int nt,
                             int ctas_per_sm);
 
+/* lrnr_set_wait_limit -- iteration cap of the tensor-core kernel's mbarrier waits
+ * (tensor-core MMA completion and bulk-copy arrival; the paper has no counterpart):
+ * `polls` >= 0 polls per wait (each poll may block briefly in the barrier), < 0 =
+ * the default (2^20).  A wait that reaches the cap records LRNR_ETIMEOUT in the
+ * device status (lrnr_last_device_status) and the kernel returns after waiting,
+ * with a fixed bound of its own, for the MMAs and copies it still has outstanding;
+ * no other state is changed.  A cap of 0 makes every call time out: it exists to
+ * exercise that path. */
+lrnr_status lrnr_set_wait_limit(lrnr_model *m, int64_t polls);
+
 /* lrnr_model_info -- host outputs (any may be NULL): L, M, sum_r, sum_m and
  * whether every hidden layer has reduced bases (fast_ready). */
 lrnr_status lrnr_model_info(const lrnr_model *m, int *L, int *M, int *sum_r, int *sum_m,

@@ -68,6 +68,7 @@ _SIGS = {
     "lrnr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lrnr_destroy": (None, [_P]),
     "lrnr_measure_peaks": (ctypes.c_int, [_P, _P]),
+    "lrnr_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
 }
 
 EXPORTS = tuple(_SIGS)
@@ -171,6 +172,11 @@ def lrnr_set_tuning(model: Model, form: str, prec: str, nt: int = 0, ctas_per_sm
     """Override the launch shape for (form, prec); 0 = automatic."""
     _check(lib().lrnr_set_tuning(model.handle, _FORM[form], _PREC[prec], int(nt), int(ctas_per_sm)),
            "lrnr_set_tuning")
+
+
+def lrnr_set_wait_limit(model: Model, polls: int = -1):
+    """Iteration cap of the tensor-core kernel's waits (polls per wait; -1 = default)."""
+    _check(lib().lrnr_set_wait_limit(model.handle, int(polls)), "lrnr_set_wait_limit")
 
 
 def lrnr_timing(model: Model, enable: bool = True):

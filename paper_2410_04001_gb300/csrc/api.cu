@@ -64,6 +64,7 @@ struct lrnr_model {
   size_t ev_used = 0;
   std::vector<cudaEvent_t> cap_start, cap_stop;
   // launch-shape overrides per (form, precision): points per tile, CTAs per SM cap
+  uint32_t wait_limit = 1u << 20;              // mbarrier poll cap of the tensor-core kernel
   int tune_nt[2][4] = {{0}};
   int tune_cta[2][4] = {{0}};
   // tickets of the two-level Adam reduction and of the FastLRNR kernel's fused
@@ -389,7 +390,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     p.rows = m->rows_dev;
     p.sum_m = m->sum_m;
   }
-  p.max_wait = 1u << 20;
+  p.max_wait = m->wait_limit;
   p.loss = LRNR_LOSS_MSE;
   p.w[0] = p.w[1] = p.w[2] = 1.0f;
   return LRNR_OK;
@@ -836,6 +837,12 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   lrnr_status rc = ensure_tickets(m, tiles / kRedGroup + 2 + 2 * (int64_t)max_inst, nullptr);
   if (rc != LRNR_OK) return rc;
   return ensure_ws(m, need, nullptr);
+}
+
+lrnr_status lrnr_set_wait_limit(lrnr_model *m, int64_t polls) {
+  if (!m) return LRNR_EINVAL;
+  m->wait_limit = polls < 0 ? (1u << 20) : (uint32_t)std::min<int64_t>(polls, UINT32_MAX);
+  return LRNR_OK;
 }
 
 lrnr_status lrnr_set_tuning(lrnr_model *m, lrnr_form form, lrnr_precision prec, int nt,

@@ -80,11 +80,16 @@ struct TcLayout {
 };
 
 // All threads wait for `bar` to complete the phase with parity `ph`; false (and the
-// device status set) if the wait timed out.
-__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, const KParams &p) {
+// device status set) if the wait timed out.  The expected parity advances only on
+// success, so that after a timeout the drain at the end of the kernel waits for the
+// very phase (the MMA or copy still in flight) that timed out.
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, bool &pend, const KParams &p) {
   const bool ok = tc::mbar_wait(bar, ph, p.max_wait);
-  ph ^= 1u;
   const bool all = __syncthreads_and(ok);
+  if (all) {
+    ph ^= 1u;
+    pend = false;
+  }
   if (!all && threadIdx.x == 0) set_status(p.status, DEV_TIMEOUT);
   tc::fence_after_sync();
   return all;
@@ -149,6 +154,9 @@ struct Ctl {
   uint64_t *b1, *b2, *bb;   // GEMM barriers, B-buffer barriers [NB]
   uint32_t ph1, ph2, phb[2];
   int chunk_ctr;            // chunks consumed so far (selects the B buffer)
+  // an MMA commit or a copy is outstanding on the barrier (uniform over the CTA): the
+  // drain after a timeout waits for exactly these
+  bool p1, p2, pb[2];
 };
 
 template <int RM, int PREC, int C, int NC>
@@ -221,8 +229,11 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   auto fetch = [&](const unsigned char *lp, int j, int n) {
     if (tid == 0)
       bulk_copy(bbuf(n), lp + (size_t)j * PK::CHUNK, Lay::BBYTES, &ctl.bb[n % Lay::NB]);
+    ctl.pb[n % Lay::NB] = true;
   };
-  auto wait_b = [&](int n) { return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], p); };
+  auto wait_b = [&](int n) {
+    return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], ctl.pb[n % Lay::NB], p);
+  };
 
   // ---------------- forward (the operand A1 of layer l >= 1 is written at the end
   // of layer l - 1, from its rank-r result)
@@ -241,7 +252,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     fetch(lp, 0, n0);
     for (int j = 0; j < NCH; ++j) {
       const int n = n0 + j;
-      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }   // GEMM2(j-1) done
+      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }   // GEMM2(j-1) done
       if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
       if (!wait_b(n)) { dead = true; return; }
       if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
@@ -259,7 +270,8 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
                                 SBO_R, ID_W, kk > 0);
         tc::mma_commit(ctl.b1);
       }
-      if (!wait_bar(ctl.b1, ctl.ph1, p)) { dead = true; return; }
+      ctl.p1 = true;
+      if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
       const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
       {
         const int c0 = half * HC;
@@ -309,9 +321,10 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
                                 SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
         tc::mma_commit(ctl.b2);
       }
+      ctl.p2 = true;
     }
     ctl.chunk_ctr = n0 + NCH;
-    if (!wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
+    if (!wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
     if (lead) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
@@ -384,7 +397,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     fetch(lp, 0, n0);
     for (int j = 0; j < NCH; ++j) {
       const int n = n0 + j;
-      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
+      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
       if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
       if (!wait_b(n)) { dead = true; return; }
       if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
@@ -406,7 +419,8 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           }
         tc::mma_commit(ctl.b1);
       }
-      if (!wait_bar(ctl.b1, ctl.ph1, p)) { dead = true; return; }
+      ctl.p1 = true;
+      if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
       const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
 #pragma unroll
       for (int h8 = 0; h8 < HC / 8; ++h8) {
@@ -461,6 +475,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
                                 SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
         tc::mma_commit(ctl.b2);
       }
+      ctl.p2 = true;
       if (tid < NC) {
         // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
         const int h = tid / HC, cc = tid % HC;
@@ -471,7 +486,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       }
     }
     ctl.chunk_ctr = n0 + NCH;
-    if (!wait_bar(ctl.b2, ctl.ph2, p)) { dead = true; return; }
+    if (!wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
     if (lead) {
       // dL/ds^l = sum_c pbar_c * q_c, and the output adjoint of layer l - 1
       float g[RM];
@@ -516,7 +531,7 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_f
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tb = *tbase;
-  Ctl ctl{&bar[0], &bar[1], &bar[2], 0u, 0u, {0u, 0u}, 0};
+  Ctl ctl{&bar[0], &bar[1], &bar[2], 0u, 0u, {0u, 0u}, 0, false, false, {false, false}};
   bool dead = false;
   float *qst = p.scratch + (size_t)blockIdx.x * (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * TNT;
   const int ntiles = __ldg(p.tile_off + p.n_inst);
@@ -546,10 +561,13 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_f
     }
   }
   if (dead) {
-    // give in-flight tensor-core work and copies a bounded chance to finish
-    tc::mbar_wait(ctl.b1, ctl.ph1, p.max_wait);
-    tc::mbar_wait(ctl.b2, ctl.ph2, p.max_wait);
-    for (int b = 0; b < Lay::NB; ++b) tc::mbar_wait(&ctl.bb[b], ctl.phb[b], p.max_wait);
+    // let the MMAs and copies this CTA started finish before TMEM and shared memory
+    // are released: a fixed bound of its own, whatever the caller's wait cap
+    constexpr uint32_t kDrainPolls = 1u << 20;
+    if (ctl.p1) tc::mbar_wait(ctl.b1, ctl.ph1, kDrainPolls);
+    if (ctl.p2) tc::mbar_wait(ctl.b2, ctl.ph2, kDrainPolls);
+    for (int b = 0; b < Lay::NB; ++b)
+      if (ctl.pb[b]) tc::mbar_wait(&ctl.bb[b], ctl.phb[b], kDrainPolls);
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -131,3 +131,27 @@ def test_peak_microbenchmarks_are_plausible(P):
     assert 0.8 * formula < max(pk["fp32_fma_tflops"], pk["fp32_fma2_tflops"]) < 1.1 * formula, (pk, formula)
     assert pk["tanh_approx_gops"] > 0 and pk["tanhf_gops"] > 0 and pk["fp64_fma_tflops"] > 0
     assert 500 < pk["sm_mhz"] < 2500
+
+
+def test_wait_cap_reports_timeout_and_the_next_call_is_exact(P):
+    """Failure detection without a GPU fault: a cap of zero polls on the tensor-core
+    kernel's mbarrier waits makes its first wait give up; the kernel records
+    LRNR_ETIMEOUT, waits for the copy and MMAs it still has outstanding and returns.
+    With the cap restored the same call reproduces the earlier result bit for bit."""
+    import torch
+    g = synth.rng(78)
+    net = synth.make_net(g, L=2, M=64, r=16)
+    bt = synth.make_batch(g, net, 200, 20, 10, 5.0, 1.0, 2.0)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    db = P.DeviceBatch.from_host(bt)
+    ref = [t.clone() for t in P.lrnr_residual_grad(model, "full", "bf16", db)]
+    assert P.lrnr_last_device_status(model) == 0
+    P.lrnr_set_wait_limit(model, 0)
+    P.lrnr_residual_grad(model, "full", "bf16", db)
+    torch.cuda.synchronize()
+    assert P.lrnr_last_device_status(model) == P.binding.ETIMEOUT
+    P.lrnr_set_wait_limit(model, -1)
+    again = P.lrnr_residual_grad(model, "full", "bf16", db)
+    assert P.lrnr_last_device_status(model) == 0
+    for a, b in zip(again, ref):
+        assert torch.equal(a, b)
