@@ -16,5 +16,13 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
 * ``lrnr64.cdr_residual``   pinned: three closed-form solutions of Eq. 4.1.
 * ``eim64.eim_greedy``      pinned: scaled unit vectors, unit lower-triangular
   ``P^T Xi``, exact interpolation of spanned snapshots, brute-force rule replay.
+* ``deim64.pod_basis``      pinned: planted spectrum (known singular vectors and
+  values, rank cut); eigenvectors of ``S S^T`` and the Eckart-Young projection
+  error, both against a symmetric eigen-solver.
+* ``deim64.deim_rows``      pinned: equal to the pivot order of LU with partial
+  pivoting (LAPACK); unit-vector bases; tie rule; exact interpolation of the span
+  and the DEIM bound on ``||(P^T Xi)^{-1}||``; invariance to column scaling and
+  equivariance under row relabelling; reduced network exact at the snapshot points
+  and equal to the full network when every row is kept.
 * ``adam64.adam_step``      pinned: ``torch.optim.Adam`` in FP64.
 """
