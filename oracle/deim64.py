@@ -17,7 +17,9 @@ Eq. 2.7 leaves the basis Xi and the sampling matrix P open.  In the DEIM reading
         c = (P_{j-1}^T Xi_{j-1})^{-1} P_{j-1}^T xi_j,
     and take p_j = argmax_i |xi_j(i) - (Xi_{j-1} c)(i)| (lowest index among exact
     ties).  The residual vanishes on the rows already chosen, so the rows are
-    distinct and P^T Xi is invertible.
+    distinct and P^T Xi is invertible.  A residual whose largest magnitude is at most
+    1e-12 of the column's own largest entry (rounding level: the column lies in the
+    span of the earlier ones) stops the selection with an error.
 
 Then the reduced layer is Eq. 2.7 with this (Xi, P).  P^T Xi is invertible but, unlike
 the EIM basis, not triangular, so V-hat takes a general solve
@@ -26,6 +28,9 @@ the EIM basis, not triangular, so V-hat takes a general solve
 from __future__ import annotations
 
 import numpy as np
+
+
+DEPENDENT = 1e-12   # relative residual at which a basis column counts as dependent
 
 
 def canonical_signs(Xi: np.ndarray) -> np.ndarray:
@@ -66,7 +71,7 @@ def deim_rows(Xi: np.ndarray) -> np.ndarray:
             c = np.linalg.solve(Xi[P, :j], xj[P])
             res = xj - Xi[:, :j] @ c
         p = int(np.argmax(np.abs(res)))       # first occurrence: lowest index among ties
-        if p in rows or not np.abs(res[p]) > 0.0:
+        if p in rows or not np.abs(res[p]) > DEPENDENT * np.max(np.abs(xj)):
             raise np.linalg.LinAlgError("DEIM: the basis columns are not independent")
         rows.append(p)
     return np.array(rows, dtype=np.int64)

@@ -151,3 +151,13 @@ def test_fast_network_with_deim_on_every_row_is_the_full_network():
     uf, _ = O.full_forward(net, s, x2, t2)
     uh, _ = O.fast_forward(fnet, s, x2, t2)
     assert relerr(uh, uf) < 1e-10
+
+
+def test_deim_rejects_a_dependent_column():
+    g = synth.rng(340)
+    Xi = g.standard_normal((30, 4))
+    Xi[:, 3] = 2.0 * Xi[:, 1] - Xi[:, 0]
+    with pytest.raises(np.linalg.LinAlgError):
+        D.deim_rows(Xi)
+    Xi[:, 3] += 1e-9 * g.standard_normal(30)     # independent, if barely
+    assert len(set(D.deim_rows(Xi).tolist())) == 4
