@@ -380,6 +380,58 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
     del model, db, dsub
     out["paper_d1_fast_phase"] = paper_fast_phase(P, synth, np, torch, dev)
     out["paper_d2_fast_phase_bf16"] = paper_fast_phase(P, synth, np, torch, dev, d2=True)
+    out["eim_vs_deim_rhat_sweep"] = eim_vs_deim(P, synth, np, torch, dev)
+    return out
+
+
+def eim_vs_deim(P, synth, np, torch, dev):
+    """Accuracy of the reduced network against the full one as a function of rhat,
+    for the two ways of choosing (Xi, P) in Eq. 2.7: greedy EIM on the snapshots and
+    POD + DEIM.  Metric: mean absolute difference u_FAST - u_LRNR over a uniform
+    256 x 64 grid of the domain (the measure of Fig. 2), at the coefficients the
+    snapshots were taken around (s0) and at s0 perturbed by 5 % (unseen); FP32
+    kernels, snapshots from 8 coefficient draws around s0 at the 4 x 3 design plus
+    8 perturbations per point."""
+    xg, tg = np.meshgrid(np.linspace(0, 2 * np.pi, 256), np.linspace(0, 1, 64), indexing="ij")
+    out = {}
+    cases = (("cdr_M256_r16_L5", synth.workload_cdr_single()[0], 1005),
+             ("paper_d1_M4000_r(1,5,5,3,1)", synth.workload_paper_d1()[0], 1006))
+    for name, net, seed in cases:
+        g = synth.rng(seed)
+        model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+        s0 = synth.make_s(g, 1, sum(net.r))[0]
+        draws = np.stack([s0] + [s0 * (1.0 + 0.1 * g.standard_normal(s0.shape)) for _ in range(7)])
+        s1 = s0 * (1.0 + 0.05 * g.standard_normal(s0.shape))
+        xs, ts = synth.snapshot_design(synth.rng(77), 8)
+        xs_d, ts_d = torch.tensor(xs, device=dev), torch.tensor(ts, device=dev)
+        S = [P.lrnr_snapshots(model, l, xs_d, ts_d, torch.tensor(draws, device=dev))
+             for l in range(net.L)]
+        grid = lambda s: P.DeviceBatch.from_host(synth.Batch(
+            beta=np.array([1.0]), nu=np.array([0.0]), rho=np.array([0.0]), s=s[None, :],
+            int_off=np.array([0, xg.size]), ic_off=np.array([0, 0]), bc_off=np.array([0, 0]),
+            x_int=xg.ravel(), t_int=tg.ravel(), x_ic=np.zeros(0), t_bc=np.zeros(0)), dev)
+        batches = {"s0": grid(s0), "s0_perturbed_5pct": grid(s1)}
+        ref = {k: P.lrnr_residual(model, "full", "fp32", b)["u"].double() for k, b in batches.items()}
+        rows = []
+        for rh in (2, 4, 6, 8, 12, 16):
+            row = {"rhat": rh}
+            for method in ("eim", "deim"):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for l in range(net.L):
+                    if method == "eim":
+                        P.fastlrnr_select_rows(model, l, S[l], rh)
+                    else:
+                        P.fastlrnr_select_rows_deim(model, l, S[l], rh, n_iter=20)
+                e1.record()
+                torch.cuda.synchronize()
+                row[method + "_select_ms"] = e0.elapsed_time(e1)
+                for k, b in batches.items():
+                    uf = P.lrnr_residual(model, "fast", "fp32", b)["u"].double()
+                    row[f"{method}_mae_{k}"] = float((uf - ref[k]).abs().mean())
+            rows.append(row)
+        out[name] = {"mean_abs_u_LRNR_s0": float(ref["s0"].abs().mean()), "sweep": rows}
+        del model
     return out
 
 

@@ -145,6 +145,42 @@ lrnr_status fastlrnr_select_rows(lrnr_model *m, int layer, const double *snapsho
                                  int *rhat_used, void *stream);
 
 /*
+ * lrnr_pod -- POD basis of a snapshot matrix: the leading left singular vectors
+ * Xi of S, the basis of the DEIM reading of Sec. 2.2 Eq. 2.7.  FP64 throughout.
+ *   snapshots: device FP64 M x K, column-major, not modified.  n_modes: 1..32
+ *   (at most min(M, K) are returned).  Method: block subspace iteration on S S^T
+ *   with nb = min(M, K, 64, max(n_modes + 8, 2 n_modes)) columns, started from
+ *   S times a K x nb sign matrix (a fixed counter hash), n_iter (0..1000)
+ *   iterations Q <- orth(S (S^T Q)), then Rayleigh-Ritz on (S^T Q)^T (S^T Q) by
+ *   cyclic Jacobi.  Accuracy of mode j grows like (sigma_{nb+1} / sigma_j)^(2 n_iter).
+ *   Each returned column is scaled by +-1 so that its entry of largest magnitude
+ *   (lowest index among exact ties) is positive.  Modes with sigma_j <= tol * sigma_1
+ *   (0 <= tol < 1) are dropped.
+ *   Outputs: basis_out device FP64 M x n_modes column-major (the first *n_used
+ *   columns are written); sigma_out device FP64 [n_modes] or NULL; resid_out
+ *   device FP64 [n_modes] or NULL: ||S S^T xi_j - sigma_j^2 xi_j||_2 / sigma_1^2 of
+ *   each returned mode; *n_used (host, may be NULL).
+ *   Allocates scratch ((M + K) * nb doubles and split partials), synchronises
+ *   `stream`, runs on the current device.  LRNR_ETIMEOUT if the Jacobi sweeps do
+ *   not converge (cap 64 sweeps), LRNR_ESINGULAR if orthonormalisation fails.
+ */
+lrnr_status lrnr_pod(const double *snapshots, int M, int64_t K, int n_modes, int n_iter,
+                     double tol, double *basis_out, double *sigma_out, double *resid_out,
+                     int *n_used, void *stream);
+
+/*
+ * lrnr_deim_rows -- DEIM index selection (the sampling matrix P of Sec. 2.2
+ * Eq. 2.7 for a given basis): p_1 = argmax_i |xi_1(i)|; step j solves
+ * (P^T Xi_{j-1}) c = P^T xi_j (Gaussian elimination, partial pivoting, FP64) and
+ * takes p_j = argmax_i |xi_j(i) - (Xi_{j-1} c)(i)|, lowest index among exact ties.
+ *   basis: device FP64 M x n column-major (n 1..32, n <= M); rows_out: device
+ *   int32 [n].  LRNR_ESINGULAR when the columns are dependent (a zero residual or
+ *   pivot), LRNR_ENONFINITE on NaN.  Synchronises `stream`.  The rows and basis are
+ *   what fastlrnr_select_rows takes as rows_in / Xi_in.
+ */
+lrnr_status lrnr_deim_rows(const double *basis, int M, int n, int32_t *rows_out, void *stream);
+
+/*
  * lrnr_residual -- forward only (Sec. 2.1 Eq. 2.1 / Sec. 2.2 Eq. 2.8 and Eq. 4.1).
  * Writes, for interior points, u, u_t, u_x, u_xx and the residual N[u] (device
  * FP32 [n_int] each), the initial residual u(x,0) - sin x (device [n_ic]) and the

@@ -9,4 +9,5 @@ from .binding import (DeviceBatch, LrnrError, Model, fastlrnr_select_rows, lrnr_
                       lrnr_destroy, lrnr_last_device_status, lrnr_model_info, lrnr_reserve,
                       lrnr_residual, lrnr_residual_grad, lrnr_snapshots, lrnr_status_string,
                       lrnr_residual_grad_noalloc, lrnr_set_tuning, lrnr_timing, lrnr_timing_read, spinprop_step,
-                      lrnr_measure_peaks, lrnr_set_wait_limit)
+                      lrnr_measure_peaks, lrnr_set_wait_limit, lrnr_pod, lrnr_deim_rows,
+                      fastlrnr_select_rows_deim)

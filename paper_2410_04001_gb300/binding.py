@@ -69,6 +69,9 @@ _SIGS = {
     "lrnr_destroy": (None, [_P]),
     "lrnr_measure_peaks": (ctypes.c_int, [_P, _P]),
     "lrnr_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lrnr_pod": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, _P, _P, _P, _P, _P]),
+    "lrnr_deim_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
 }
 
 EXPORTS = tuple(_SIGS)
@@ -290,6 +293,49 @@ def fastlrnr_select_rows(model: Model, layer: int, snapshots=None, rhat: int = 1
     _check(rc, "fastlrnr_select_rows")
     n = used.value
     return rows[:n], Xi[:n], n
+
+
+def lrnr_pod(snapshots, n_modes: int, n_iter: int = 30, tol: float = 1e-10, stream=None):
+    """POD modes of a snapshot matrix.  ``snapshots``: device FP64 tensor of shape
+    (K, M) (the column-major M x K matrix).  Returns (Xi of shape (n_used, M), i.e.
+    the column-major M x n_used basis, sigma (n_used,), resid (n_used,), n_used)."""
+    S = snapshots.to(torch.float64).contiguous()
+    K, M = int(S.shape[0]), int(S.shape[1])
+    n = min(int(n_modes), M, K)
+    Xi = torch.zeros((n, M), dtype=torch.float64, device=S.device)
+    sig = torch.zeros(n, dtype=torch.float64, device=S.device)
+    res = torch.zeros(n, dtype=torch.float64, device=S.device)
+    used = ctypes.c_int(0)
+    rc = lib().lrnr_pod(_ptr(S), M, K, int(n_modes), int(n_iter), float(tol), _ptr(Xi), _ptr(sig),
+                        _ptr(res), ctypes.byref(used), _stream(stream))
+    _check(rc, "lrnr_pod")
+    u = used.value
+    return Xi[:u], sig[:u], res[:u], u
+
+
+def lrnr_deim_rows(Xi, stream=None):
+    """DEIM rows of the basis ``Xi`` (device FP64, shape (n, M): column-major M x n)."""
+    Xi = Xi.to(torch.float64).contiguous()
+    n, M = int(Xi.shape[0]), int(Xi.shape[1])
+    rows = torch.full((n,), -1, dtype=torch.int32, device=Xi.device)
+    rc = lib().lrnr_deim_rows(_ptr(Xi), M, n, _ptr(rows), _stream(stream))
+    _check(rc, "lrnr_deim_rows")
+    return rows
+
+
+def fastlrnr_select_rows_deim(model: Model, layer: int, snapshots, rhat: int = 16,
+                              n_iter: int = 30, tol: float = 1e-10, stream=None):
+    """DEIM selection for one hidden layer: POD basis of the snapshots (``lrnr_pod``),
+    its DEIM rows (``lrnr_deim_rows``), then the reduced layer of Eq. 2.7 installed
+    through ``fastlrnr_select_rows`` with those rows and that basis.  Returns
+    (rows, Xi of shape (rhat_used, M), rhat_used, sigma)."""
+    Xi, sig, _, used = lrnr_pod(snapshots, rhat, n_iter=n_iter, tol=tol, stream=stream)
+    if used < 1:
+        raise LrnrError(4, "lrnr_pod: no mode above the cut")
+    rows = lrnr_deim_rows(Xi, stream=stream)
+    rows, Xi, used = fastlrnr_select_rows(model, layer, None, used, 0.0, rows_in=rows, Xi_in=Xi,
+                                          stream=stream)
+    return rows, Xi, used, sig
 
 
 def lrnr_residual(model: Model, form: str, prec: str, batch: DeviceBatch, stream=None, out=None):

@@ -6,7 +6,8 @@ coefficients, u_FASTSOL = u_LRNR(.; s_fast).
 
 This module only sequences calls of the C ABI (``liblrnr.so``); every step runs in
 its kernels: snapshots and the EIM greedy in FP64 (``lrnr_snapshots``,
-``fastlrnr_select_rows``), the SPInProp Adam steps (``spinprop_step`` with the l1
+``fastlrnr_select_rows``; or the POD basis and DEIM rows, ``lrnr_pod`` and
+``lrnr_deim_rows``), the SPInProp Adam steps (``spinprop_step`` with the l1
 loss and the locality term), and the full-width evaluation (``lrnr_residual``).
 """
 from __future__ import annotations
@@ -16,15 +17,28 @@ import torch
 from . import binding as B
 
 
-def build_reduced(model: B.Model, x, t, s_draws, rhat: int, tol: float = 0.0, stream=None):
-    """Select the EIM rows of every hidden layer from the exact-LRNR states at the
-    points (x, t) (device FP64 vectors, the sample set X and its perturbations) for
-    each coefficient vector in ``s_draws`` (n_s x sum_r); installs the reduced
-    layers in ``model`` and returns, per layer, the rows and the number kept."""
+def build_reduced(model: B.Model, x, t, s_draws, rhat: int, tol: float = 0.0, stream=None,
+                  method: str = "eim", n_iter: int = 30):
+    """Select the rows of every hidden layer from the exact-LRNR states at the points
+    (x, t) (device FP64 vectors, the sample set X and its perturbations) for each
+    coefficient vector in ``s_draws`` (n_s x sum_r); installs the reduced layers in
+    ``model`` and returns, per layer, the rows and the number kept.
+
+    ``method="eim"``: the greedy EIM of ``fastlrnr_select_rows`` (``tol`` is its
+    absolute stopping level).  ``method="deim"``: POD basis by ``lrnr_pod``
+    (``n_iter`` subspace iterations; ``tol`` is the relative singular-value cut,
+    1e-10 when 0 is passed) and DEIM rows by ``lrnr_deim_rows``."""
+    if method not in ("eim", "deim"):
+        raise ValueError(f"unknown selection method {method!r}")
     out = []
     for layer in range(model.L):
         S = B.lrnr_snapshots(model, layer, x, t, s_draws, stream=stream)
-        rows, _, used = B.fastlrnr_select_rows(model, layer, S, rhat, tol, stream=stream)
+        if method == "eim":
+            rows, _, used = B.fastlrnr_select_rows(model, layer, S, rhat, tol, stream=stream)
+        else:
+            rows, _, used, _ = B.fastlrnr_select_rows_deim(model, layer, S, rhat, n_iter=n_iter,
+                                                           tol=tol if tol > 0 else 1e-10,
+                                                           stream=stream)
         out.append((rows, used))
     return out
 
