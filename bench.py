@@ -381,6 +381,56 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
     out["paper_d1_fast_phase"] = paper_fast_phase(P, synth, np, torch, dev)
     out["paper_d2_fast_phase_bf16"] = paper_fast_phase(P, synth, np, torch, dev, d2=True)
     out["eim_vs_deim_rhat_sweep"] = eim_vs_deim(P, synth, np, torch, dev)
+    out.update(small_and_stress(P, synth, np, torch, dev, timed_steps, with_oracle))
+    return out
+
+
+def small_and_stress(P, synth, np, torch, dev, timed_steps, with_oracle):
+    """The latency case (M = 64, r = 8, L = 4, pure convection, 1,408 points: microseconds
+    per residual + gradient call, FP32 full width and FastLRNR) and the full-width
+    adjoint stress case (M = 1,024, r = 32, L = 6, 262,144 points: FP32, BF16, TF32
+    and split-BF16), each a residual + gradient call with the L2 flushed before it; dL/ds
+    of the stress case against the oracle on a 1,024-point sub-batch."""
+    out = {}
+    net, bt = synth.workload_convection_small()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    select_rows_on_device(P, model, net, bt.s[0], dev, torch, synth)
+    db = P.DeviceBatch.from_host(bt, dev)
+    r = {"workload": "M=64 r=8 L=4 convection beta=5; 1,024 + 256 + 128 pairs", "points": db.n_points}
+    for form in ("full", "fast"):
+        res = P.lrnr_residual_grad(model, form, "fp32", db)
+        ts_, _, _ = timed_steps(lambda: P.lrnr_residual_grad(model, form, "fp32", db, out=res), 50)
+        r[form + "_fp32_us_per_call"] = 1e3 * sum(ts_) / len(ts_)
+    out["latency_small_convection"] = r
+    del model, db
+    net, bt = synth.workload_adjoint_stress()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    db = P.DeviceBatch.from_host(bt, dev)
+    n = db.n_points
+    r = {"workload": "M=1024 r=32 L=6 CDR; 262,144 interior points, full width", "points": n}
+    if with_oracle:
+        from oracle import lrnr64
+        f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        sub = synth.Batch(beta=f32(bt.beta), nu=f32(bt.nu), rho=f32(bt.rho), s=f32(bt.s),
+                          int_off=np.array([0, 1024]), ic_off=np.array([0, 0]), bc_off=np.array([0, 0]),
+                          x_int=f32(bt.x_int[:1024]), t_int=f32(bt.t_int[:1024]), x_ic=np.zeros(0),
+                          t_bc=np.zeros(0))
+        _, rs, _ = lrnr64.residual_grad(net, sub, "full")
+        dsub = P.DeviceBatch.from_host(sub, dev)
+    for prec in ("fp32", "bf16", "tf32", "bf16x3"):
+        res = P.lrnr_residual_grad(model, "full", prec, db, want_db=False)
+        P.lrnr_timing(model, True)
+        ts_, km, kn = timed_steps(lambda: P.lrnr_residual_grad(model, "full", prec, db, out=res,
+                                                               want_db=False), 3, model)
+        P.lrnr_timing(model, False)
+        ms = sum(ts_) / len(ts_)
+        e = {"ms_per_call": ms, "kernel_ms": km / max(1, kn), "points_per_s": n / (ms * 1e-3)}
+        if with_oracle:
+            _, ds, _ = P.lrnr_residual_grad(model, "full", prec, dsub, want_db=False)
+            e["err_dL_ds_1024_points"] = float(np.linalg.norm(ds.cpu().numpy() - rs) / np.linalg.norm(rs))
+        r[prec] = e
+    out["full_width_adjoint_stress"] = r
+    del model, db
     return out
 
 
@@ -660,8 +710,8 @@ def main():
     # ---- variants: full-width FP32 LRNR residual + gradient, fast residual + gradient
     variants = {}
     P.lrnr_timing(model, True)
-    for form, prec in (("full", "fp32"), ("full", "bf16"), ("full", "bf16x3"), ("fast", "fp32"),
-                       ("fast", "bf16"), ("fast", "bf16x3")):
+    for form, prec in (("full", "fp32"), ("full", "bf16"), ("full", "tf32"), ("full", "bf16x3"),
+                       ("fast", "fp32"), ("fast", "bf16"), ("fast", "tf32"), ("fast", "bf16x3")):
         try:
             out = P.lrnr_residual_grad(model, form, prec, db)
         except P.LrnrError as e:
@@ -681,7 +731,9 @@ def main():
             "tflops": fl / (kms * 1e-3) / 1e12, "frac_fp32_peak": fl / (kms * 1e-3) / 1e12 / peak,
             "hbm_gbs": (n_pts * 8) / (kms * 1e-3) / 1e9}
         if prec != "fp32":
-            products = 3 if prec == "bf16x3" else 1
+            # executed tensor work in BF16-MMA equivalents: split-BF16 issues five BF16
+            # products per contraction, a TF32 MMA runs at half the BF16 rate
+            products = {"bf16": 1, "tf32": 2, "bf16x3": 5}[prec]
             variants[f"{form}_{prec}"]["frac_bf16_peak"] = (
                 products * fl / (kms * 1e-3) / 1e12 / float(peaks.get("bf16_tflops", 1900.0)))
     P.lrnr_timing(model, False)
@@ -705,8 +757,8 @@ def main():
             assert np.array_equal(p, rows_all[l]), "EIM rows differ from the oracle"
             Xis.append(Xi)
         fnet = lrnr64.make_fast(net, rows_all, Xis)
-        for form, ref, precs in (("fast", fnet, ("fp32", "bf16", "bf16x3")),
-                                 ("full", net, ("fp32", "bf16", "bf16x3"))):
+        for form, ref, precs in (("fast", fnet, ("fp32", "bf16", "tf32", "bf16x3")),
+                                 ("full", net, ("fp32", "bf16", "tf32", "bf16x3"))):
             ro, rs, rb = lrnr64.residual_grad(ref, bt32, form)
             for prec in precs:
                 if "unavailable" in variants.get(f"{form}_{prec}", {}):

@@ -66,7 +66,9 @@ typedef enum {
 
 typedef enum {
   LRNR_FP32 = 0,        /* FP32 SIMT everywhere (reference precision of the GPU path) */
-  LRNR_TF32 = 1,        /* reserved */
+  LRNR_TF32 = 1,        /* tcgen05 kind::tf32: operands rounded to TF32 (10-bit mantissa,
+                           nearest), FP32 accumulation in TMEM (both forms; ranks up
+                           to 32) */
   LRNR_BF16 = 2,        /* tcgen05 BF16 operands, FP32 accumulation in TMEM (both forms;
                            the reduced network is an LRNR of width rhat, Sec. 2.2 Eq. 2.8) */
   LRNR_BF16X3 = 3       /* split-BF16: activations hi + lo, bases hi + mid + lo, products

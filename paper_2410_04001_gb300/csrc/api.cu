@@ -18,11 +18,11 @@ cudaError_t launch_snapshots_f64(const double *w64, int L, int M, const int *r_d
                                  const int64_t *offs_dev, int layer, int64_t n_pts,
                                  const double *x, const double *t, int n_s, const double *s,
                                  int sum_r, double *out, cudaStream_t st);
-int full_tc_supported(int L, int M, int RM, int NC, int split);
-size_t full_tc_pack_bytes(int L, int M, int RM, int NC);
+int full_tc_supported(int L, int M, int RM, int NC, int prec);
+size_t full_tc_pack_bytes(int L, int M, int RM, int NC, int tf32);
 void full_tc_pack(int L, int M, int RM, int NC, const std::vector<std::vector<double>> &U,
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
-                  const int *r, std::vector<unsigned char> &out);
+                  const int *r, std::vector<unsigned char> &out, int tf32);
 int full_tc_nt();
 size_t full_tc_scratch_floats(int L, int RM, int grid);
 }  // namespace lrnr
@@ -44,6 +44,8 @@ struct lrnr_model {
   int64_t *offs_dev = nullptr;
   void *tc_pack = nullptr;                     // tensor-core operand pack (full form)
   void *ftc_pack = nullptr;                    // tensor-core pack of the reduced network
+  void *tf_pack = nullptr;                     // the same two packs in TF32
+  void *ftf_pack = nullptr;
   int ftc_nc = 16;                             // its chunk width (32 at rank 64)
   // reduced layers (host, FP64): Uh [rh][r_l], bh [rh], Vh [rh][r_{l+1}], rows [rh]
   int rhat[LMAX] = {0};
@@ -117,6 +119,11 @@ int64_t max_tiles(int64_t n_int, int64_t n_ic, int64_t n_bc, int n_inst, int nt)
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Precisions that run on the tensor cores.
+bool tc_prec(lrnr_precision prec) {
+  return prec == LRNR_BF16 || prec == LRNR_BF16X3 || prec == LRNR_TF32;
+}
 
 lrnr_status ensure_ws(lrnr_model *m, size_t need, cudaStream_t st) {
   if (m->ws_bytes >= need) return LRNR_OK;
@@ -204,10 +211,12 @@ lrnr_status build_fast_pack(lrnr_model *m) {
   // (Eq. 2.8): pack it for the tensor-core kernel in 16-column chunks, rows past
   // rhat zero (they contribute nothing and get a zero dL/db).
   if (m->ftc_pack) cudaFree(m->ftc_pack);
+  if (m->ftf_pack) cudaFree(m->ftf_pack);
   m->ftc_pack = nullptr;
+  m->ftf_pack = nullptr;
   const int RMt = std::max(16, RMp);
   m->ftc_nc = RMt <= 32 ? 16 : 32;
-  if (full_tc_supported(L, RHp, RMt, m->ftc_nc, 0)) {
+  if (full_tc_supported(L, RHp, RMt, m->ftc_nc, LRNR_BF16)) {
     std::vector<std::vector<double>> Ur(L + 1), Vr(L + 1), br(L + 1);
     Vr[0] = m->V[0];
     Ur[L] = m->U[L];
@@ -224,9 +233,14 @@ lrnr_status build_fast_pack(lrnr_model *m) {
       }
     }
     std::vector<unsigned char> tp;
-    full_tc_pack(L, RHp, RMt, m->ftc_nc, Ur, Vr, br, m->r, tp);
+    full_tc_pack(L, RHp, RMt, m->ftc_nc, Ur, Vr, br, m->r, tp, 0);
     CK(cudaMalloc(&m->ftc_pack, tp.size()));
     CK(cudaMemcpy(m->ftc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice));
+    if (full_tc_supported(L, RHp, RMt, m->ftc_nc, LRNR_TF32)) {
+      full_tc_pack(L, RHp, RMt, m->ftc_nc, Ur, Vr, br, m->r, tp, 1);
+      CK(cudaMalloc(&m->ftf_pack, tp.size()));
+      CK(cudaMemcpy(m->ftf_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice));
+    }
   }
   m->fast_dirty = false;
   return LRNR_OK;
@@ -269,12 +283,12 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   p.x_int = bt->x_int; p.t_int = bt->t_int; p.x_ic = bt->x_ic; p.t_bc = bt->t_bc;
   p.grad = grad ? 1 : 0;
   p.status = m->status_dev;
-  if (form == LRNR_FAST && (prec == LRNR_BF16 || prec == LRNR_BF16X3)) {
+  if (form == LRNR_FAST && tc_prec(prec)) {
     // the reduced network on the tensor cores: an LRNR of width RH
     rc = build_fast_pack(m);
     if (rc != LRNR_OK) return rc;
-    if (!m->ftc_pack || !full_tc_supported(m->L, m->fRH, std::max(16, m->fRM), m->ftc_nc,
-                                           prec == LRNR_BF16X3))
+    if (!(prec == LRNR_TF32 ? m->ftf_pack : m->ftc_pack) ||
+        !full_tc_supported(m->L, m->fRH, std::max(16, m->fRM), m->ftc_nc, prec))
       return LRNR_ENOTSUP;
     p.RM = std::max(16, m->fRM);
     p.RH = m->fRH;
@@ -315,9 +329,10 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
           full_fp32_smem_bytes(m->L, p.RM, tn, partial_len(m->L, p.RM, m->L * m->M + 1)) <=
               (size_t)kSmemBudget)
         p.nt = tn;
-    } else if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
+    } else if (tc_prec(prec)) {
       p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
-      if (!m->tc_pack || !full_tc_supported(m->L, m->M, p.RM, 32, prec == LRNR_BF16X3))
+      if (!(prec == LRNR_TF32 ? m->tf_pack : m->tc_pack) ||
+          !full_tc_supported(m->L, m->M, p.RM, 32, prec))
         return LRNR_ENOTSUP;
       p.pack = nullptr;
       p.nt = full_tc_nt();
@@ -331,7 +346,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   p.P = grad ? partial_len(m->L, p.RM, ps.nb_entries - 1) : 0;
   const int64_t tiles = max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, p.nt);
   if (tiles > INT32_MAX / 2) return LRNR_EINVAL;
-  const bool tc = prec == LRNR_BF16 || prec == LRNR_BF16X3;
+  const bool tc = tc_prec(prec);
   ps.grid_cap = (int)std::min<int64_t>(tiles, INT32_MAX);
   size_t scr_bytes = 0;
   if (tc) {
@@ -424,10 +439,11 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
     ++m->ev_used;
     CK(cudaEventRecord(e1, st));
   }
-  if (prec == LRNR_BF16 || prec == LRNR_BF16X3) {
+  if (tc_prec(prec)) {
     const bool fast = form == LRNR_FAST;
-    CK(launch_full_tc(p, fast ? m->ftc_pack : m->tc_pack, (int)prec, fast ? m->ftc_nc : 32,
-                      ps.grid_cap, st));
+    const void *pk = prec == LRNR_TF32 ? (fast ? m->ftf_pack : m->tf_pack)
+                                       : (fast ? m->ftc_pack : m->tc_pack);
+    CK(launch_full_tc(p, pk, (int)prec, fast ? m->ftc_nc : 32, ps.grid_cap, st));
   } else if (form == LRNR_FAST) {
     CK(launch_fast(p, ps.grid_cap, st));
   } else {
@@ -546,11 +562,17 @@ lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U, const
   if ((e = cudaMemcpy(m->offs_dev, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc(&m->status_dev, sizeof(int))) != cudaSuccess) return fail(e);
   if ((e = cudaMemset(m->status_dev, 0, sizeof(int))) != cudaSuccess) return fail(e);
-  if (full_tc_supported(L, M, std::max(16, RM), 32, 0)) {
+  if (full_tc_supported(L, M, std::max(16, RM), 32, LRNR_BF16)) {
     std::vector<unsigned char> tp;
-    full_tc_pack(L, M, std::max(16, RM), 32, m->U, m->V, m->b, m->r, tp);
+    full_tc_pack(L, M, std::max(16, RM), 32, m->U, m->V, m->b, m->r, tp, 0);
     if ((e = cudaMalloc(&m->tc_pack, tp.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(m->tc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  }
+  if (full_tc_supported(L, M, std::max(16, RM), 32, LRNR_TF32)) {
+    std::vector<unsigned char> tp;
+    full_tc_pack(L, M, std::max(16, RM), 32, m->U, m->V, m->b, m->r, tp, 1);
+    if ((e = cudaMalloc(&m->tf_pack, tp.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(m->tf_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   }
   *out = m;
   return LRNR_OK;
@@ -930,6 +952,8 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->offs_dev);
   cudaFree(m->tc_pack);
   cudaFree(m->ftc_pack);
+  cudaFree(m->tf_pack);
+  cudaFree(m->ftf_pack);
   cudaFree(m->fast_pack);
   cudaFree(m->rows_dev);
   cudaFree(m->status_dev);

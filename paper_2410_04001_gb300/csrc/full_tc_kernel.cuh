@@ -1,0 +1,625 @@
+// Full-width LRNR residual + adjoint on the tcgen05 tensor cores (Sec. 2.1
+// Eq. 2.1-2.2, Sec. 2.3), BF16, TF32 or split-BF16 operands with FP32 accumulation
+// in tensor memory.  The kernel template; its BF16 / split-BF16 instantiations and
+// the host-side packing are in full_tc.cu, the TF32 ones in full_tc_tf32.cu.
+//
+// A CTA owns a tile of 128 collocation points; point p is TMEM lane p.  For every
+// hidden layer the M-wide activation is produced and consumed in chunks of NC = 32
+// columns, never stored whole (a width-chunked two-GEMM fusion):
+//   forward   a_c  = (s * q_c) U_chunk^T            GEMM1  (M=128, N=NC, K=r)
+//             z_c  = tanh jet of a (+ bias)          epilogue, CUDA cores, FP32
+//             q'_c += z_c Vn_chunk                   GEMM2  (M=128, N=r, K=NC)
+//   reverse   a_c  = (s * q_c) U_chunk^T            GEMM1  (recomputed)
+//             zb_c = qb'_c Vn_chunk^T                GEMM3  (M=128, N=NC, K=r)
+//             ab_c = adjoint of the tanh jet         epilogue; column sums give dL/db
+//             pb_c += ab_c U_chunk                   GEMM4  (M=128, N=r, K=NC)
+// with one MMA per jet channel c (value, d/dt, d/dx, d2/dx2).  Split-BF16 keeps the
+// activations as hi + lo and the bases as hi + mid + lo (exact to 2^-24) and
+// accumulates five BF16 products per contraction.  TF32 (kind::tf32) takes 32-bit
+// operands rounded to a 10-bit mantissa: twice the shared memory and half the K of a
+// BF16 MMA, so twice the MMAs per contraction.
+//
+// Eight warps: warps w and w+4 share TMEM lanes 32(w%4).. and split each chunk's
+// epilogue columns; warps 0-3 also do the per-point work.  Thread 0 issues the
+// MMAs and the bulk copies.  The bases are packed chunk by chunk in the operand
+// layout (no-swizzle K-major core matrices) so that one cp.async.bulk moves a
+// chunk; chunk j+1 is copied while chunk j is processed (two buffers when shared
+// memory allows).  The rank-r layer inputs q (FP32) are kept in a per-CTA global
+// scratch area (it stays in L2) for the reverse sweep.  Every mbarrier wait is
+// bounded.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lrnr_internal.cuh"
+#include "point_common.cuh"
+#include "simt_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace lrnr {
+namespace {
+
+constexpr int TNT = 128;   // points per tile = TMEM lanes
+constexpr int NTH = 256;   // threads: two per point (column halves of a chunk)
+// NC: hidden-width chunk, 32 (full-width networks: one CTA and 512 TMEM columns per
+// SM) or 16 (narrow networks such as the FastLRNR reduced layers: two CTAs and 256
+// TMEM columns each per SM, so that one CTA's epilogue overlaps the other's MMAs; with
+// rank 64 the rank-r accumulators alone take 256 columns and one CTA runs per SM).
+template <int NC, int RM>
+constexpr int tmem_cols() { return (NC == 16 && RM <= 32) ? 256 : 512; }
+
+// Chunk block of the packed bases (bytes), three equal groups of PIECE bytes: the
+// hi pieces of Ub (NC x RM), Vb (NC x RM), Utb (RM x NC), Vtb (RM x NC) followed by
+// the chunk's biases (NC floats); then the mid pieces; then the lo pieces.
+// A TF32 pack (ES = 4 bytes per element) holds one piece per chunk.
+template <int RM, int NC, int ES = 2>
+struct Pk {
+  static constexpr int T = NC * RM * ES;
+  static constexpr int PIECE = 4 * T + 4 * NC;      // offset from a hi tile to its mid tile
+  static constexpr int HI = PIECE;                  // bytes needed by BF16 and TF32
+  static constexpr int ALL = 3 * PIECE;             // bytes needed by split-BF16
+  static constexpr int CHUNK = ES == 4 ? PIECE : ALL;
+};
+
+// Operand precision of the kernel: 1 = BF16, 2 = TF32, 3 = split-BF16.
+template <int PREC>
+constexpr int elem_bytes() { return PREC == 2 ? 4 : 2; }
+
+template <int RM, int PREC, int NC>
+struct TcLayout {
+  static constexpr int HC = NC / 2;                 // columns per epilogue thread
+  static constexpr int ES = elem_bytes<PREC>();     // bytes per operand element
+  static constexpr int KPM = 32 / ES;               // K elements per MMA (32 bytes of a row)
+  static constexpr int PARTS = PREC == 3 ? 2 : 1;   // activation pieces
+  static constexpr int A1B = TNT * RM * ES;         // one (channel, piece) rank-r operand
+  static constexpr int A24B = TNT * NC * ES;        // one (channel, piece) width operand
+  static constexpr int BBYTES = PREC == 3 ? Pk<RM, NC>::ALL : Pk<RM, NC, ES>::HI;
+  static constexpr int OFF_A1 = 0;
+  static constexpr int OFF_A3 = OFF_A1 + 4 * PARTS * A1B;
+  static constexpr int OFF_A24 = OFF_A3 + 4 * PARTS * A1B;
+  static constexpr int OFF_B = OFF_A24 + 4 * PARTS * A24B;
+  static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
+  static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
+  static constexpr int OFF_F = OFF_B + NB * BSTRIDE;
+  // float area: s [(L+1)*RM], red [4][PL] (loss, dL/ds, output-bias dL/db), dbw [8][HC];
+  // then the mbarriers and the TMEM base address
+  static __host__ __device__ int floats(int L) { return (L + 1) * RM + 4 * (2 + (L + 1) * RM) + 8 * HC; }
+  static __host__ __device__ int bytes(int L) { return OFF_F + floats(L) * 4 + 128; }
+};
+
+// All threads wait for `bar` to complete the phase with parity `ph`; false (and the
+// device status set) if the wait timed out.  The expected parity advances only on
+// success, so that after a timeout the drain at the end of the kernel waits for the
+// very phase (the MMA or copy still in flight) that timed out.
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, bool &pend, const KParams &p) {
+  const bool ok = tc::mbar_wait(bar, ph, p.max_wait);
+  const bool all = __syncthreads_and(ok);
+  if (all) {
+    ph ^= 1u;
+    pend = false;
+  }
+  if (!all && threadIdx.x == 0) set_status(p.status, DEV_TIMEOUT);
+  tc::fence_after_sync();
+  return all;
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
+// Store 8 consecutive K entries (k0 a multiple of 8) of one row of a K-major operand
+// with K columns: BF16 (and, for split-BF16, the rounded remainder into the lo piece)
+// or TF32 (round to nearest).
+template <int PREC>
+__device__ __forceinline__ void put8(unsigned char *hi_base, unsigned char *lo_base, int row,
+                                     int k0, int K, const float (&w)[8]) {
+  if constexpr (PREC == 2) {
+    *reinterpret_cast<uint4 *>(hi_base + tc::kmajor_off_e(row, k0, K, 4)) =
+        tc::pack4_tf32(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(hi_base + tc::kmajor_off_e(row, k0 + 4, K, 4)) =
+        tc::pack4_tf32(w[4], w[5], w[6], w[7]);
+  } else {
+    uint4 hi, lo;
+    tc::pack8_bf16(w, hi, lo);
+    const uint32_t off = tc::kmajor_off(row, k0, K);
+    *reinterpret_cast<uint4 *>(hi_base + off) = hi;
+    if constexpr (PREC == 3) *reinterpret_cast<uint4 *>(lo_base + off) = lo;
+  }
+}
+
+// Write a rank-r row (this thread's point) of channel c into a K-major operand.
+template <int RM, int PREC, int NC>
+__device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const float *v, int row) {
+  using Lay = TcLayout<RM, PREC, NC>;
+#pragma unroll
+  for (int k0 = 0; k0 < RM; k0 += 8) {
+    float w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = v[k0 + i];
+    put8<PREC>(base + (Lay::PARTS * c) * Lay::A1B, base + (2 * c + 1) * Lay::A1B, row, k0, RM, w);
+  }
+}
+
+// D (+)= A B^T with A = Ah (+ Al) and B = Bh (+ Bm + Bl) in BF16 pieces.  BF16:
+// Ah Bh.  Split: Ah Bh + Ah Bm + Al Bh + Ah Bl + Al Bm; the dropped terms are below
+// 2^-25 relative, and the error left is that of the two-piece activation.  TF32: one
+// product of TF32 operands.
+template <int RM, int PREC, int NC>
+__device__ __forceinline__ void mma_split(uint32_t d, uint32_t aHi, uint32_t aLo, uint32_t b,
+                                          uint32_t sboA, uint32_t sboB, uint32_t idesc,
+                                          uint32_t acc) {
+  const uint64_t ah = tc::sdesc(aHi, 128, sboA);
+  if constexpr (PREC == 2) {
+    tc::mma_tf32(d, ah, tc::sdesc(b, 128, sboB), idesc, acc);
+    return;
+  }
+  tc::mma_bf16(d, ah, tc::sdesc(b, 128, sboB), idesc, acc);
+  if constexpr (PREC == 3) {
+    constexpr uint32_t PC = Pk<RM, NC>::PIECE;
+    const uint64_t al = tc::sdesc(aLo, 128, sboA);
+    const uint64_t bm = tc::sdesc(b + PC, 128, sboB);
+    tc::mma_bf16(d, ah, bm, idesc, 1u);
+    tc::mma_bf16(d, al, tc::sdesc(b, 128, sboB), idesc, 1u);
+    tc::mma_bf16(d, ah, tc::sdesc(b + 2 * PC, 128, sboB), idesc, 1u);
+    tc::mma_bf16(d, al, bm, idesc, 1u);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void act_jet(float a0, float &z, float &d1, float &d2) {
+  z = (PREC == 1) ? tc::tanh_approx(a0) : tanhf(a0);
+  d1 = 1.0f - z * z;
+  d2 = -2.0f * z * d1;
+}
+
+struct Ctl {
+  uint64_t *b1, *b2, *bb;   // GEMM barriers, B-buffer barriers [NB]
+  uint32_t ph1, ph2, phb[2];
+  int chunk_ctr;            // chunks consumed so far (selects the B buffer)
+  // an MMA commit or a copy is outstanding on the barrier (uniform over the CTA): the
+  // drain after a timeout waits for exactly these
+  bool p1, p2, pb[2];
+};
+
+template <int RM, int PREC, int C, int NC>
+__device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char *sm,
+                        const unsigned char *__restrict__ pack, float *__restrict__ qst,
+                        uint32_t tb, Ctl &ctl, bool &dead) {
+  using Lay = TcLayout<RM, PREC, NC>;
+  using PK = Pk<RM, NC, Lay::ES>;
+  constexpr int KPM = Lay::KPM;
+  constexpr int HC = NC / 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (TNT - 1);       // point / TMEM lane
+  const int half = tid >> 7;             // column half of the epilogue
+  const bool lead = tid < TNT;           // threads doing the per-point work
+  const int L = p.L, M = p.M;
+  const int NCH = (M + NC - 1) / NC;
+  unsigned char *sA1 = sm + Lay::OFF_A1;
+  unsigned char *sA3 = sm + Lay::OFF_A3;
+  unsigned char *sA24 = sm + Lay::OFF_A24;
+  unsigned char *sB0 = sm + Lay::OFF_B;
+  float *fa = reinterpret_cast<float *>(sm + Lay::OFF_F);
+  const float *s_s = fa;
+  const int PL = 2 + (L + 1) * RM;
+  float *red_w = fa + (L + 1) * RM + (warp & 3) * PL;
+  float *dbw = fa + (L + 1) * RM + 4 * PL;
+  const float *tail = reinterpret_cast<const float *>(pack + (size_t)L * NCH * PK::CHUNK);
+  const float Uout = tail[2 * R1], bout = tail[2 * R1 + 1];
+  const uint32_t sA1u = tc::smem_u32(sA1), sA3u = tc::smem_u32(sA3), sA24u = tc::smem_u32(sA24);
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const uint32_t D1 = tb, D3 = tb + 4 * NC, D24 = tb + 8 * NC;
+  constexpr uint32_t ID_W = PREC == 2 ? tc::idesc_tf32(128, NC) : tc::idesc_bf16(128, NC);
+  constexpr uint32_t ID_R = PREC == 2 ? tc::idesc_tf32(128, RM) : tc::idesc_bf16(128, RM);
+  // byte stride between 8-row core-matrix groups: K elements of ES bytes, 8 rows
+  constexpr uint32_t SBO_R = RM * Lay::ES * 8, SBO_W = NC * Lay::ES * 8;
+
+  const PointIn pt = load_point(p, T, row);
+  // Rank-r jets are handled one channel at a time (RM floats live at a time): the
+  // input jet of layer 0, the rank-r accumulator in TMEM, the layer-input store.
+  auto input_jet_c = [&](int c, float (&v)[RM]) {
+#pragma unroll
+    for (int k = 0; k < RM; ++k) v[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < R1; ++k) {
+      if (c == 0) v[k] = tail[k] * pt.x + tail[R1 + k] * pt.t;
+      else if (c == 1) v[k] = tail[R1 + k];
+      else if (c == 2) v[k] = tail[k];
+    }
+  };
+  auto rank_c = [&](int c, float (&v)[RM]) {
+#pragma unroll
+    for (int k0 = 0; k0 < RM; k0 += 16) {
+      float w[16];
+      tc::tmem_ld16(D24 + lane_base + c * RM + k0, w);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[k0 + i] = w[i];
+    }
+  };
+  auto stored_c = [&](int l, int c, float (&v)[RM]) {   // input jet of layer l >= 1
+#pragma unroll
+    for (int k = 0; k < RM; ++k) v[k] = qst[(((l - 1) * 4 + c) * RM + k) * TNT + row];
+  };
+  auto put_scaled = [&](unsigned char *base, int c, const float (&v)[RM], int l) {
+    float y[RM];
+#pragma unroll
+    for (int k = 0; k < RM; ++k) y[k] = v[k] * s_s[l * RM + k];
+    put_rank_row<RM, PREC, NC>(base, c, y, row);
+  };
+  auto bbuf = [&](int n) { return sB0 + (n % Lay::NB) * Lay::BSTRIDE; };
+  // Stream the chunks of a layer through the B buffers: before chunk j, chunk j+1
+  // (or, with one buffer, chunk j itself) is requested.
+  auto fetch = [&](const unsigned char *lp, int j, int n) {
+    if (tid == 0)
+      bulk_copy(bbuf(n), lp + (size_t)j * PK::CHUNK, Lay::BBYTES, &ctl.bb[n % Lay::NB]);
+    ctl.pb[n % Lay::NB] = true;
+  };
+  auto wait_b = [&](int n) {
+    return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], ctl.pb[n % Lay::NB], p);
+  };
+
+  // ---------------- forward (the operand A1 of layer l >= 1 is written at the end
+  // of layer l - 1, from its rank-r result)
+  if (lead) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float v[RM];
+      input_jet_c(c, v);
+      put_scaled(sA1, c, v, 0);
+    }
+  }
+  float qL[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // the last layer's rank-1 result, per channel
+  for (int l = 0; l < L && !dead; ++l) {
+    const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
+    const int n0 = ctl.chunk_ctr;
+    fetch(lp, 0, n0);
+    for (int j = 0; j < NCH; ++j) {
+      const int n = n0 + j;
+      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }   // GEMM2(j-1) done
+      if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
+      if (!wait_b(n)) { dead = true; return; }
+      if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+      const uint32_t sB = tc::smem_u32(bbuf(n));
+      tc::fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int kk = 0; kk < RM / KPM; ++kk)
+            mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
+                                SBO_R, ID_W, kk > 0);
+        tc::mma_commit(ctl.b1);
+      }
+      ctl.p1 = true;
+      if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+      const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
+      {
+        const int c0 = half * HC;
+        float a[C][HC];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          if constexpr (HC == 16) tc::tmem_ld16(D1 + lane_base + c * NC + c0, a[c]);
+          else tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
+        }
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < HC; ++i) {
+          float z, d1, d2;
+          act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
+          if constexpr (C == 4) {
+            a[3][i] = d2 * a[2][i] * a[2][i] + d1 * a[3][i];
+            a[1][i] *= d1;
+            a[2][i] *= d1;
+          }
+          a[0][i] = z;
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int h = 0; h < HC / 8; ++h) {
+            float w8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
+            put8<PREC>(sA24 + (Lay::PARTS * c) * Lay::A24B, sA24 + (2 * c + 1) * Lay::A24B, row,
+                       c0 + h * 8, NC, w8);
+          }
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int kk = 0; kk < NC / KPM; ++kk)
+            mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
+                                sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 3 * PK::T + kk * 256,
+                                SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+        tc::mma_commit(ctl.b2);
+      }
+      ctl.p2 = true;
+    }
+    ctl.chunk_ctr = n0 + NCH;
+    if (!wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
+    if (lead) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        float v[RM];
+        rank_c(c, v);
+        if (l + 1 < L) {
+          if (p.grad) {
+#pragma unroll
+            for (int k = 0; k < RM; ++k) qst[((l * 4 + c) * RM + k) * TNT + row] = v[k];
+          }
+          put_scaled(sA1, c, v, l + 1);
+        } else {
+          qL[c] = v[0];
+        }
+      }
+    }
+    tc::fence_before_sync();
+  }
+  float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float sL = s_s[L * RM];
+  if (lead) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) u[c] = Uout * sL * qL[c];
+    u[0] += bout;
+  }
+  float ub[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lpv = 0.0f;
+  bool go = false;
+  if (lead) go = residual_and_seeds(p, T, pt, row, u, ub, lpv);
+  if (!__syncthreads_or(go)) return;      // evaluation mode: done
+
+  // ---------------- reverse sweep
+  const int DB0 = partial_db0(L, RM);
+  float *prow = p.partial + (int64_t)tile * p.P;
+  if (lead) {
+    // loss, dL/ds of the linear output layer, dL/db of the output bias
+    const float ls = warp_sum(lpv);
+    float dsL = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) dsL += Uout * ub[c] * qL[c];
+    const float s0 = warp_sum(dsL);
+    const float s1 = warp_sum(ub[0]);
+    if (lane == 0) {
+      red_w[0] += ls;
+      red_w[1 + L * RM] += s0;
+      red_w[PL - 1] += s1;
+    }
+    // A3 of the last hidden layer: the output adjoint seeds
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float qb[RM];
+#pragma unroll
+      for (int k = 0; k < RM; ++k) qb[k] = 0.0f;
+      qb[0] = sL * Uout * ub[c];
+      put_rank_row<RM, PREC, NC>(sA3, c, qb, row);
+    }
+  }
+  // (A3 of layer l < L - 1 is written at the end of layer l + 1: pbar * s^(l+1))
+  for (int l = L - 1; l >= 0 && !dead; --l) {
+    const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
+    if (lead) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        float v[RM];
+        if (l > 0) stored_c(l, c, v);
+        else input_jet_c(c, v);
+        put_scaled(sA1, c, v, l);
+      }
+    }
+    const int n0 = ctl.chunk_ctr;
+    fetch(lp, 0, n0);
+    for (int j = 0; j < NCH; ++j) {
+      const int n = n0 + j;
+      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
+      if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
+      if (!wait_b(n)) { dead = true; return; }
+      if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+      const uint32_t sB = tc::smem_u32(bbuf(n));
+      tc::fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int kk = 0; kk < RM / KPM; ++kk) {
+            mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
+                                SBO_R, ID_W, kk > 0);
+            mma_split<RM, PREC, NC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                sA3u + (2 * c + 1) * Lay::A1B + kk * 256, sB + PK::T + kk * 256,
+                                SBO_R, SBO_R, ID_W, kk > 0);
+          }
+        tc::mma_commit(ctl.b1);
+      }
+      ctl.p1 = true;
+      if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+      const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
+#pragma unroll
+      for (int h8 = 0; h8 < HC / 8; ++h8) {
+        const int c0 = half * HC + h8 * 8;
+        float a[C][8], wb[C][8];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
+          tc::tmem_ld8(D3 + lane_base + c * NC + c0, wb[c]);
+        }
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float z, d1, d2;
+          act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
+          float ab0 = wb[0][i] * d1;
+          if constexpr (C == 4) {
+            const float d3 = d1 * (6.0f * z * z - 2.0f);
+            ab0 += d2 * (wb[1][i] * a[1][i] + wb[2][i] * a[2][i]) +
+                   wb[3][i] * (d3 * a[2][i] * a[2][i] + d2 * a[3][i]);
+            wb[2][i] = wb[2][i] * d1 + 2.0f * wb[3][i] * d2 * a[2][i];
+            wb[3][i] = wb[3][i] * d1;
+            wb[1][i] = wb[1][i] * d1;
+          }
+          wb[0][i] = ab0;
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          put8<PREC>(sA24 + (Lay::PARTS * c) * Lay::A24B, sA24 + (2 * c + 1) * Lay::A24B, row, c0,
+                     NC, wb[c]);
+        float g8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) g8[i] = wb[0][i];
+        const float r = warp_reduce_scatter<8>(g8);
+        if ((lane & 3) == 0) dbw[warp * HC + h8 * 8 + (lane >> 2)] = r;
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int kk = 0; kk < NC / KPM; ++kk)
+            mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
+                                sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 2 * PK::T + kk * 256,
+                                SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+        tc::mma_commit(ctl.b2);
+      }
+      ctl.p2 = true;
+      if (tid < NC) {
+        // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
+        const int h = tid / HC, cc = tid % HC;
+        const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
+                        dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
+        const int col = j * NC + tid;
+        if (col < M) prow[DB0 + l * M + col] = v;
+      }
+    }
+    ctl.chunk_ctr = n0 + NCH;
+    if (!wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
+    if (lead) {
+      // dL/ds^l = sum_c pbar_c * q_c, and the output adjoint of layer l - 1
+      float g[RM];
+#pragma unroll
+      for (int k = 0; k < RM; ++k) g[k] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        float pb[RM], v[RM];
+        rank_c(c, pb);
+        if (l > 0) stored_c(l, c, v);
+        else input_jet_c(c, v);
+#pragma unroll
+        for (int k = 0; k < RM; ++k) g[k] = fmaf(pb[k], v[k], g[k]);
+        if (l > 0) put_scaled(sA3, c, pb, l);
+      }
+      warp_accumulate<RM>(g, red_w, [&](int jj) { return 1 + l * RM + jj; });
+    }
+    tc::fence_before_sync();
+  }
+}
+
+template <int RM, int PREC, int NC>
+__global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_full_tc(const __grid_constant__ KParams p,
+                                                  const unsigned char *__restrict__ pack) {
+  using Lay = TcLayout<RM, PREC, NC>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x;
+  const int L = p.L;
+  float *fa = reinterpret_cast<float *>(sm + Lay::OFF_F);
+  float *s_s = fa;
+  const int PL = 2 + (L + 1) * RM;
+  float *red_s = fa + (L + 1) * RM;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((Lay::OFF_F + Lay::floats(L) * 4 + 15) & ~15));
+  uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
+  if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC, RM>());
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
+    tc::fence_mbar_init();
+  }
+  if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tb = *tbase;
+  Ctl ctl{&bar[0], &bar[1], &bar[2], 0u, 0u, {0u, 0u}, 0, false, false, {false, false}};
+  bool dead = false;
+  float *qst = p.scratch + (size_t)blockIdx.x * (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * TNT;
+  const int ntiles = __ldg(p.tile_off + p.n_inst);
+  for (int tile = blockIdx.x; tile < ntiles && !dead; tile += gridDim.x) {
+    const Tile T = decode_tile(p, tile);
+    __syncthreads();
+    for (int j = tid; j < (L + 1) * RM; j += NTH) {
+      const int l = j / RM, k = j % RM;
+      s_s[j] = (k < p.r[l]) ? __ldg(p.s + (int64_t)T.inst * p.sum_r + p.roff[l] + k) : 0.0f;
+    }
+    for (int j = tid; j < 4 * PL; j += NTH) red_s[j] = 0.0f;
+    __syncthreads();
+    if (T.kind == KIND_INT)
+      tc_tile<RM, PREC, 4, NC>(p, T, tile, sm, pack, qst, tb, ctl, dead);
+    else
+      tc_tile<RM, PREC, 1, NC>(p, T, tile, sm, pack, qst, tb, ctl, dead);
+    if (dead) break;
+    if (p.grad) {
+      __syncthreads();
+      for (int j = tid; j < PL; j += NTH) {
+        const float acc = red_s[j] + red_s[PL + j] + red_s[2 * PL + j] + red_s[3 * PL + j];
+        if (j == 0 && !isfinite(acc)) set_status(p.status, DEV_NONFINITE);
+        // entries 0 .. PL-2 are the loss and dL/ds; the last is the output-bias dL/db
+        const int dst = j < PL - 1 ? j : partial_db0(L, RM) + L * p.M;
+        p.partial[(int64_t)tile * p.P + dst] = acc;
+      }
+    }
+  }
+  if (dead) {
+    // let the MMAs and copies this CTA started finish before TMEM and shared memory
+    // are released: a fixed bound of its own, whatever the caller's wait cap
+    constexpr uint32_t kDrainPolls = 1u << 20;
+    if (ctl.p1) tc::mbar_wait(ctl.b1, ctl.ph1, kDrainPolls);
+    if (ctl.p2) tc::mbar_wait(ctl.b2, ctl.ph2, kDrainPolls);
+    for (int b = 0; b < Lay::NB; ++b)
+      if (ctl.pb[b]) tc::mbar_wait(&ctl.bb[b], ctl.phb[b], kDrainPolls);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid < 32) tc::tmem_dealloc(tb, tmem_cols<NC, RM>());
+}
+
+template <int RM, int PREC, int NC>
+cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaStream_t st) {
+  using Lay = TcLayout<RM, PREC, NC>;
+  const size_t bytes = (size_t)Lay::bytes(p.L);
+  cudaError_t e = cudaFuncSetAttribute(k_full_tc<RM, PREC, NC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // every CTA holds tmem_cols<NC, RM>() TMEM columns: at most 512 / that many per SM
+  const int grid = std::max(1, std::min(grid_cap, sms * (512 / tmem_cols<NC, RM>())));
+  k_full_tc<RM, PREC, NC><<<grid, NTH, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
+  return cudaGetLastError();
+}
+
+template <int RM, int NC, int ES = 2>
+int pk_chunk() { return Pk<RM, NC, ES>::CHUNK; }
+
+}  // namespace
+}  // namespace lrnr

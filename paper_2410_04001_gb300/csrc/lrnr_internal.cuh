@@ -250,6 +250,8 @@ cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st);
 // NC: 32-column chunks (full-width networks, one CTA per SM) or 16-column chunks
 // (narrow networks, two CTAs per SM while RM <= 32).
+cudaError_t launch_full_tc_tf32(const KParams &p, const void *tc_pack, int NC, int grid_cap,
+                                cudaStream_t st);
 cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int NC, int grid_cap,
                            cudaStream_t st);
 cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,

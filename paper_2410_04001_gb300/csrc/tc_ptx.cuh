@@ -1,5 +1,5 @@
 // Thin inline-PTX wrappers for the Blackwell (sm_100a / sm_103a) tensor-core path:
-// tensor memory (TMEM) allocation, tcgen05.mma with BF16 operands and FP32
+// tensor memory (TMEM) allocation, tcgen05.mma with BF16 or TF32 operands and FP32
 // accumulation, commit to an mbarrier, TMEM loads, and the fences that order them
 // against ordinary shared-memory traffic.
 //
@@ -24,6 +24,13 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k, int K) {
   return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// The same for elements of es bytes (2: BF16, 4: TF32): a core matrix row is 16
+// bytes, i.e. 16 / es consecutive K elements.
+__host__ __device__ __forceinline__ uint32_t kmajor_off_e(int row, int k, int K, int es) {
+  const int per = 16 / es;
+  return (uint32_t)((row >> 3) * (K * es * 8) + (k / per) * 128 + (row & 7) * 16 + (k % per) * es);
+}
+
 // Shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
 // byte offsets, descriptor version 1, no swizzle.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -38,6 +45,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 // Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, dense.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, dense.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
@@ -61,6 +74,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// D[tmem] (+)= A * B^T with TF32 operands, one instruction (M x N x 8).
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -160,6 +184,15 @@ __device__ __forceinline__ void pack8_bf16(const float (&v)[8], uint4 &hi, uint4
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Four floats rounded to TF32 (nearest, ties away from zero), as 16 bytes.
+__device__ __forceinline__ uint4 pack4_tf32(float a, float b, float c, float d) {
+  uint32_t r[4];
+  const float v[4] = {a, b, c, d};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r[i]) : "f"(v[i]));
+  return make_uint4(r[0], r[1], r[2], r[3]);
 }
 
 // Round-to-nearest-even BF16 split: x = hi + lo with hi = rn(x), lo = rn(x - hi).
