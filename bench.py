@@ -661,6 +661,7 @@ def main():
     torch.cuda.synchronize()
     P.lrnr_timing(model, True)
     P.lrnr_timing_read(model)
+    step_counter[0] = 0          # the first timed step is one of the eager, event-timed ones
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
