@@ -1,5 +1,7 @@
 // Tile schedule, fixed-order reduction of per-tile partial sums, and the fused
 // Adam step on s (Sec. 2.3 gradient assembly; Sec. 3.2 Eq. 3.7; Sec. 4 Adam).
+#include <cooperative_groups.h>
+
 #include "lrnr_internal.cuh"
 
 namespace lrnr {
@@ -257,6 +259,106 @@ __global__ void __launch_bounds__(256) k_reduce_adam2(const __grid_constant__ Ad
   }
 }
 
+// Cluster form of the reduction + Adam (one cluster of kClRed CTAs per instance):
+// CTA c of the cluster sums the instance's tile rows t0 + c + kClRed * m in COLS-wide
+// column slices (1024 / COLS row phases per CTA, one round of up to 16 loads per
+// thread for the batches it is used for), adds its row phases in order into a
+// shared row, and CTA 0 adds the kClRed shared rows through distributed shared
+// memory in rank order before the Adam update.  No tickets, no second pass over
+// global memory; every sum is taken in a fixed order.
+constexpr int kClRed = 8;
+constexpr int kClThreads = 1024;
+
+template <int COLS>
+__global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
+    k_reduce_adam_cl(const __grid_constant__ AdamArgs A) {
+  namespace cg = cooperative_groups;
+  constexpr int PH = kClThreads / COLS;          // row phases per CTA
+  cg::cluster_group cl = cg::this_cluster();
+  const RedArgs &a = A.red;
+  __shared__ float part[PH][COLS];
+  __shared__ float tot[COLS];
+  __shared__ float gsh[(LMAX + 1) * RMAX];
+  __shared__ float lsum[kClThreads / 32];
+  const int i = blockIdx.x / kClRed;
+  const int crank = (int)cl.block_rank();
+  const int tid = threadIdx.x, col = tid % COLS, ph = tid / COLS;
+  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
+  const int DB0 = 1 + (a.L + 1) * a.RM;
+  // CTA 0 starts reading s, m, v (and the anchor) of its Adam entries now
+  float sv = 0.0f, mv0 = 0.0f, vv0 = 0.0f, an = 0.0f;
+  const int64_t o = (int64_t)i * a.sum_r + tid;
+  const bool adam_lane = crank == 0 && tid < a.sum_r;
+  if (adam_lane) {
+    sv = A.s[o];
+    mv0 = A.m[o];
+    vv0 = A.v[o];
+    if (A.anchor) an = A.anchor[o];
+  }
+  float acc = 0.0f;
+  if (col < DB0) {
+    constexpr int STEP = kClRed * PH;             // distance between this thread's rows
+    for (int t = t0 + crank + kClRed * ph; t < t1; t += 16 * STEP) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int tq = t + q * STEP;
+        v[q] = tq < t1 ? __ldg(a.partial + (int64_t)tq * a.P + col) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc += v[q];
+    }
+  }
+  part[ph][col] = acc;
+  __syncthreads();
+  if (tid < COLS) {
+    float s2 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PH; ++q) s2 += part[q][tid];
+    tot[tid] = s2;
+  }
+  cl.sync();
+  if (crank == 0) {
+    for (int j = tid; j < DB0; j += kClThreads) {
+      float g = 0.0f;
+      for (int r = 0; r < kClRed; ++r) g += cl.map_shared_rank(tot, r)[j];
+      if (j == 0) part[0][0] = g;
+      else {
+        const int l = (j - 1) / a.RM, k = (j - 1) % a.RM;
+        if (k < a.r[l]) gsh[a.roff[l] + k] = g;
+      }
+    }
+  }
+  // every CTA's shared row stays alive until CTA 0 has read it
+  cl.sync();
+  if (crank != 0) return;
+  const int64_t k = *A.step;
+  const float bc1 = 1.0f - powf(A.b1, (float)k);
+  const float bc2 = 1.0f - powf(A.b2, (float)k);
+  float loc = 0.0f;
+  if (adam_lane) {
+    float gr = gsh[tid];
+    if (A.anchor) {
+      const float d = sv - an;
+      loc = A.lam * fabsf(d);
+      gr += A.lam * (float)((d > 0.0f) - (d < 0.0f));
+    }
+    const float mv = A.b1 * mv0 + (1.0f - A.b1) * gr;
+    const float vv = A.b2 * vv0 + (1.0f - A.b2) * gr * gr;
+    A.m[o] = mv;
+    A.v[o] = vv;
+    A.s[o] = sv - A.lr * (mv / bc1) / (sqrtf(vv / bc2) + A.eps);
+  }
+  loc = warp_sum(loc);
+  if ((tid & 31) == 0) lsum[tid >> 5] = loc;
+  __syncthreads();
+  if (tid == 0) {
+    float lt = 0.0f;
+    for (int w = 0; w < kClThreads / 32; ++w) lt += lsum[w];
+    if (a.loss_out) a.loss_out[i] = part[0][0] + lt;
+  }
+}
+
 void fill_red(RedArgs &a, const KParams &p, int n_needed, int fast, const int32_t *rows,
               float *loss_out, float *dL_ds, float *dL_db, int sum_m) {
   a.partial = p.partial;
@@ -312,7 +414,13 @@ cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, c
   A.eps = eps;
   A.lam = lam;
   A.anchor = anchor;
-  if (gsum && cnt) {
+  const int DB0 = 1 + (p.L + 1) * p.RM;
+  if (p.sum_r <= kClThreads && DB0 <= 256 && (int64_t)p.n_inst * kClRed <= INT32_MAX) {
+    if (DB0 <= 128)
+      k_reduce_adam_cl<128><<<p.n_inst * kClRed, kClThreads, 0, st>>>(A);
+    else
+      k_reduce_adam_cl<256><<<p.n_inst * kClRed, kClThreads, 0, st>>>(A);
+  } else if (gsum && cnt) {
     k_reduce_adam2<<<dim3(p.n_inst, kAdamGroups), 256, 0, st>>>(A, gsum, cnt);
   } else {
     k_reduce_adam<<<p.n_inst, dim3(32, 32), 0, st>>>(A);
