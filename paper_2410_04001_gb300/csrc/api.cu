@@ -783,7 +783,7 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec, co
     rc = run_main(m, form, prec, ps, st);
     if (rc != LRNR_OK) return rc;
     CK(launch_reduce_adam(ps.p, s_inout, adam_m, adam_v, step, lr, beta1, beta2, eps, lambda_loc,
-                          s_anchor, loss_out, ps.gsum, m->adam_cnt, st));
+                          s_anchor, loss_out, ps.gsum, m->adam_cnt, m->num_sms, st));
   }
   return LRNR_OK;
 }

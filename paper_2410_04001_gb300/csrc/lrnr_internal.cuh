@@ -257,12 +257,14 @@ cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int 
 cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,
                           int rows_stride, float *loss_out, float *dL_ds, float *dL_db,
                           int sum_m, cudaStream_t st);
-// gsum (n_inst x groups x entries floats) and cnt (n_inst zeroed ints) select the
-// two-level reduction; with nullptr the one-block-per-instance kernel runs.
+// Batches of a few instances (at most 2 * num_sms / 8) reduce with one 8-CTA
+// cluster per instance; otherwise gsum (n_inst x groups x entries floats) and cnt
+// (n_inst zeroed ints) select the two-level reduction, and with nullptr the
+// one-block-per-instance kernel runs.
 cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
                                float lr, float b1, float b2, float eps, float lam,
                                const float *anchor, float *loss_out, float *gsum, int *cnt,
-                               cudaStream_t st);
+                               int num_sms, cudaStream_t st);
 size_t adam_group_floats(int n_inst, int L, int RM);
 cudaError_t launch_eim_greedy(double *R, int M, int64_t K, int rhat, double tol, int32_t *rows,
                               double *Xi, int *used_dev, double *colmax, int64_t *colarg,

@@ -37,20 +37,22 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *io, const 
 }
 
 // Sum of column j over the rows t0 + g, t0 + g + 32, ... < t1 of the partial
-// matrix, with four independent accumulators so that several loads are in flight;
-// the order of the additions is fixed.
+// matrix, in row order; the loads of up to 16 rows are issued before their
+// additions (one L2 round trip per 16 rows).
 __device__ __forceinline__ float column_sum(const float *__restrict__ part, int P, int j, int t0,
                                             int t1, int g) {
-  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-  int t = t0 + g;
-  for (; t + 96 < t1; t += 128) {
-    a0 += __ldg(part + (int64_t)t * P + j);
-    a1 += __ldg(part + (int64_t)(t + 32) * P + j);
-    a2 += __ldg(part + (int64_t)(t + 64) * P + j);
-    a3 += __ldg(part + (int64_t)(t + 96) * P + j);
+  float acc = 0.0f;
+  for (int t = t0 + g; t < t1; t += 16 * 32) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int tq = t + 32 * q;
+      v[q] = tq < t1 ? __ldg(part + (int64_t)tq * P + j) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc += v[q];
   }
-  for (; t < t1; t += 32) a0 += __ldg(part + (int64_t)t * P + j);
-  return (a0 + a1) + (a2 + a3);
+  return acc;
 }
 
 struct RedArgs {
@@ -401,7 +403,7 @@ cudaError_t launch_reduce(const KParams &p, int n_needed, int form_fast, const i
 cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
                                float lr, float b1, float b2, float eps, float lam,
                                const float *anchor, float *loss_out, float *gsum, int *cnt,
-                               cudaStream_t st) {
+                               int num_sms, cudaStream_t st) {
   AdamArgs A;
   fill_red(A.red, p, 1 + (p.L + 1) * p.RM, 0, nullptr, loss_out, nullptr, nullptr, 0);
   A.s = s;
@@ -415,7 +417,9 @@ cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, c
   A.lam = lam;
   A.anchor = anchor;
   const int DB0 = 1 + (p.L + 1) * p.RM;
-  if (p.sum_r <= kClThreads && DB0 <= 256 && (int64_t)p.n_inst * kClRed <= INT32_MAX) {
+  // the cluster form pays off while the clusters fit in about two waves of the grid;
+  // many instances already give the two-level form enough parallelism
+  if (p.sum_r <= kClThreads && DB0 <= 256 && (int64_t)p.n_inst * kClRed <= 2 * (int64_t)num_sms) {
     if (DB0 <= 128)
       k_reduce_adam_cl<128><<<p.n_inst * kClRed, kClThreads, 0, st>>>(A);
     else

@@ -287,6 +287,44 @@ def test_spinprop_steps_match_oracle_adam(P, form):
         assert abs(lo[i].item() - lr_) <= 1e-4 * abs(lr_) + 1e-7, i
 
 
+def test_spinprop_beyond_one_grid_round_matches_oracle_adam(P):
+    """Two instances with more tiles than one round of the FastLRNR grid (so the
+    reduction and Adam run as the separate cluster kernel, not inside the tile
+    kernel), with the locality term: s after 4 steps and the last loss against the
+    oracle's Adam loop."""
+    g = synth.rng(23)
+    net = synth.make_net(g, L=3, M=32, r=8)
+    bt = as_f32_batch(synth.make_batch(g, net, [31000, 11000], [700, 300], [300, 129],
+                                       [5.0, 2.0], [1.0, 0.5], [2.0, 0.0]))
+    rows, Xis, _ = eim_for(net, bt.s[0], 16)
+    fnet = lrnr64.make_fast(net, rows, Xis)
+    model, db = make(P, net, bt)
+    install_fast(P, model, rows, Xis)
+    assert db.n_points > 2 * 152 * 128
+    s = torch.tensor(bt.s, dtype=torch.float32, device="cuda")
+    anchor = s.clone()
+    m, v = torch.zeros_like(s), torch.zeros_like(s)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lo = torch.zeros(bt.n_inst, dtype=torch.float32, device="cuda")
+    n, lr, lam = 4, 1e-2, 1e-3
+    P.spinprop_step(model, "fast", "fp32", db, s, m, v, step, n_steps=n, lr=lr, lambda_loc=lam,
+                    s_anchor=anchor, loss_out=lo)
+    assert step.item() == n
+    for i in range(bt.n_inst):
+        inst = bt.instance(i)
+
+        def lg(sv, inst=inst):
+            d = dict(inst)
+            d["s"] = sv
+            l_, g_, _ = lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet, d)
+            return l_, g_
+        sr, _, _, lr_ = adam64.spinprop_loop(lg, inst["s"], n, lr=lr, lam=lam, anchor=inst["s"])
+        disp = np.abs(sr - inst["s"]).max()
+        assert np.max(np.abs(s[i].cpu().numpy() - sr)) <= 1e-3 * disp + 1e-6, i
+        assert abs(lo[i].item() - lr_) <= 1e-4 * abs(lr_) + 1e-7, i
+    assert P.lrnr_last_device_status(model) == 0
+
+
 # --------------------------------------------------------------------- full-size
 
 def test_cdr_single_full_size_fast_and_full(P):
