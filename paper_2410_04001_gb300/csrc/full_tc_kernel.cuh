@@ -178,9 +178,14 @@ __device__ __forceinline__ void mma_split(uint32_t d, uint32_t aHi, uint32_t aLo
 
 template <int PREC>
 __device__ __forceinline__ void act_jet(float a0, float &z, float &d1, float &d2) {
-  z = (PREC == 1) ? tc::tanh_approx(a0) : tanhf(a0);
-  d1 = 1.0f - z * z;
-  d2 = -2.0f * z * d1;
+  if constexpr (PREC == 1) {
+    // BF16 operands: the MUFU tanh (about 2^-11 relative) is below their rounding
+    z = tc::tanh_approx(a0);
+    d1 = 1.0f - z * z;
+    d2 = -2.0f * z * d1;
+  } else {
+    tanh_d(a0, z, d1, d2);   // the FP32 kernels' tanh jet (errors of a few 1e-7)
+  }
 }
 
 struct Ctl {

@@ -225,10 +225,20 @@ __device__ __forceinline__ void l2_discard(const void *base, size_t bytes) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(b + o) : "memory");
 }
 
-// tanh jet: value, first, second, third derivative (tanhf, not an approximation).
+// tanh jet: value z = tanh(a), first derivative d1 = 1 - z^2 and second d2 = -2 z d1,
+// from the identity tanh|a| = 1 - q with q = 2 / (exp(2|a|) + 1) in (0, 1], so that
+// 1 - z^2 = q (2 - q) keeps its relative accuracy where tanh saturates.  exp on the
+// MUFU unit (ex2.approx, relative error about 2^-22) and its reciprocal: z has an
+// absolute error of a few 1e-7 (relative for |a| >= 0.5), d1 a relative error of a
+// few 1e-7.  Large |a| overflows exp to +inf, whose reciprocal is +0 (z = +-1, d1 =
+// 0); a NaN input stays NaN.
 __device__ __forceinline__ void tanh_d(float a, float &z, float &d1, float &d2) {
-  z = tanhf(a);
-  d1 = 1.0f - z * z;
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(a) * 2.88539008177792681f));   // 2 / ln 2
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
+  const float q = 2.0f * r;
+  z = copysignf(1.0f - q, a);
+  d1 = q * (2.0f - q);
   d2 = -2.0f * z * d1;
 }
 
