@@ -57,7 +57,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per launch of the FastLRNR kernel on this workload, from
 # one ncu capture of the current kernel (profiles/k_fast_cdr_single_m256_r16.md): the
 # mean of three launches of dram__bytes_read.sum + dram__bytes_write.sum.
-K_FAST_DRAM_BYTES = 53_167_104
+K_FAST_DRAM_BYTES = 53_415_424
 
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128
