@@ -173,29 +173,39 @@ def cpu_baseline_child():
         _, gs, _ = lrnr64.instance_loss_grad(lrnr64.fast_forward, lrnr64.fast_backward, fnet,
                                              dict(inst, s=s))
         s, m, v = adam64.adam_step(s, m, v, k, gs)
-        if time.perf_counter() - t0 > 12.0 or k >= 50:
+        if time.perf_counter() - t0 > float(os.environ.get("LRNR_CPU_SECONDS", "12")) or k >= 50:
             break
     dt = time.perf_counter() - t0
     print(json.dumps({"value": n_pts * k / dt, "steps": k, "seconds": dt, "points": n_pts}))
 
 
-def run_cpu_baseline():
-    cores = len(os.sched_getaffinity(0))
+def _cpu_child(threads, seconds):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = str(cores)
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
+    env["LRNR_CPU_SECONDS"] = str(seconds)
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child"],
                        capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
     line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
-    if not line:
+    return (json.loads(line[-1]), None) if line else (None, r.stderr[-300:])
+
+
+def run_cpu_baseline():
+    """The oracle's step on the host cores: all of them (the reported value) and one
+    BLAS thread (reported beside it)."""
+    cores = len(os.sched_getaffinity(0))
+    d, err = _cpu_child(cores, 12)
+    if d is None:
         return {"value": None, "unit": "points/s", "cores": cores, "kind": "oracle",
-                "sample": "failed: " + r.stderr[-300:]}
-    d = json.loads(line[-1])
+                "sample": "failed: " + err}
+    d1, _ = _cpu_child(1, 6)
     return {"value": d["value"], "unit": "points/s", "cores": cores, "kind": "oracle",
+            "value_1_thread": d1["value"] if d1 else None,
             "sample": (f"FP64 NumPy oracle, FastLRNR SPInProp step (residual + gradient + Adam) "
                        f"over the full 69,632-point batch, {d['steps']} steps in {d['seconds']:.1f} s; "
-                       f"BLAS threads = {cores}")}
+                       f"BLAS threads = {cores} (value_1_thread: the same with one BLAS thread, "
+                       f"{d1['steps'] if d1 else 0} steps)")}
 
 
 # --------------------------------------------------------------------------- reference arm
