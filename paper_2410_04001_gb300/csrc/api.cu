@@ -738,7 +738,7 @@ lrnr_status lrnr_residual_grad(lrnr_model *m, lrnr_form form, lrnr_precision pre
   KParams pr = ps.p;
   pr.M = m->M;   // dL/db is laid out by the full width (the reduced tensor-core pass ran with M = RH)
   CK(launch_reduce(pr, n_needed, form == LRNR_FAST, m->rows_dev, pr.RH, loss_out, dL_ds,
-                   dL_db, m->sum_m, st));
+                   dL_db, m->sum_m, m->num_sms, st));
   return LRNR_OK;
 }
 

@@ -266,7 +266,7 @@ cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int 
                            cudaStream_t st);
 cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const int32_t *rows,
                           int rows_stride, float *loss_out, float *dL_ds, float *dL_db,
-                          int sum_m, cudaStream_t st);
+                          int sum_m, int num_sms, cudaStream_t st);
 // Batches of a few instances (at most 2 * num_sms / 8) reduce with one 8-CTA
 // cluster per instance; otherwise gsum (n_inst x groups x entries floats) and cnt
 // (n_inst zeroed ints) select the two-level reduction, and with nullptr the

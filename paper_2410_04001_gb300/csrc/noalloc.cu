@@ -94,7 +94,7 @@ extern "C" lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batc
       e = cudaMemsetAsync(dL_db, 0, sizeof(float) * (size_t)bt->n_inst * sum_m, st);
     if (e == cudaSuccess)
       e = launch_reduce(p, dL_db ? p.P : partial_db0(p.L, p.RM), 1, rows, p.RH, loss_out, dL_ds,
-                        dL_db, sum_m, st);
+                        dL_db, sum_m, sms, st);
     if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? LRNR_ENOMEM : LRNR_ECUDA;
   }
   if (cur != dev) cudaSetDevice(cur);

@@ -361,6 +361,53 @@ __global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
   }
 }
 
+// Cluster form of the plain reduction (loss, dL/ds, dL/db): cluster (instance i,
+// column block y of 128 entries) of kClRed CTAs; CTA c sums the rows t0 + c + kClRed m
+// in 8 row phases, CTA 0 adds the CTAs' rows through distributed shared memory in rank
+// order and writes the results.
+__global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
+    k_reduce_cl(const __grid_constant__ RedArgs a) {
+  namespace cg = cooperative_groups;
+  constexpr int COLS = 128, PH = kClThreads / COLS;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ float part[PH][COLS];
+  __shared__ float tot[COLS];
+  const int i = blockIdx.x / kClRed;
+  const int crank = (int)cl.block_rank();
+  const int tid = threadIdx.x, col = tid % COLS, ph = tid / COLS;
+  const int j = blockIdx.y * COLS + col;
+  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
+  float acc = 0.0f;
+  if (j < a.n_needed) {
+    constexpr int STEP = kClRed * PH;
+    for (int t = t0 + crank + kClRed * ph; t < t1; t += 16 * STEP) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int tq = t + q * STEP;
+        v[q] = tq < t1 ? __ldg(a.partial + (int64_t)tq * a.P + j) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc += v[q];
+    }
+  }
+  part[ph][col] = acc;
+  __syncthreads();
+  if (tid < COLS) {
+    float s2 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PH; ++q) s2 += part[q][tid];
+    tot[tid] = s2;
+  }
+  cl.sync();
+  if (crank == 0 && tid < COLS && j < a.n_needed) {
+    float g = 0.0f;
+    for (int r = 0; r < kClRed; ++r) g += cl.map_shared_rank(tot, r)[tid];
+    scatter_out(a, i, j, g);
+  }
+  cl.sync();
+}
+
 void fill_red(RedArgs &a, const KParams &p, int n_needed, int fast, const int32_t *rows,
               float *loss_out, float *dL_ds, float *dL_db, int sum_m) {
   a.partial = p.partial;
@@ -392,11 +439,17 @@ cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_
 
 cudaError_t launch_reduce(const KParams &p, int n_needed, int form_fast, const int32_t *rows,
                           int /*rows_stride*/, float *loss_out, float *dL_ds, float *dL_db,
-                          int sum_m, cudaStream_t st) {
+                          int sum_m, int num_sms, cudaStream_t st) {
   RedArgs a;
   fill_red(a, p, n_needed, form_fast, rows, loss_out, dL_ds, dL_db, sum_m);
-  dim3 grid(p.n_inst, (n_needed + 31) / 32), block(32, 32);
-  k_reduce<<<grid, block, 0, st>>>(a);
+  const int64_t blocks = ((int64_t)n_needed + 127) / 128;
+  if ((int64_t)p.n_inst * kClRed * blocks <= 2 * (int64_t)num_sms) {
+    // few instances: one cluster per (instance, 128 entries), one round of loads
+    k_reduce_cl<<<dim3(p.n_inst * kClRed, (unsigned)blocks), kClThreads, 0, st>>>(a);
+  } else {
+    dim3 grid(p.n_inst, (n_needed + 31) / 32), block(32, 32);
+    k_reduce<<<grid, block, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
