@@ -328,18 +328,36 @@ def test_spinprop_beyond_one_grid_round_matches_oracle_adam(P):
 # --------------------------------------------------------------------- full-size
 
 def test_cdr_single_full_size_fast_and_full(P):
-    """The 65,536 + 2,048 + 1,024-pair CDR workload at full size, both forms,
-    in the launch configuration the benchmark times."""
+    """The 65,536 + 2,048 + 1,024-pair CDR workload at full size, both forms, every
+    precision (FP32 1e-5, split-BF16 1e-5, TF32 2.5e-3, BF16 2e-2), in the launch
+    configuration the benchmark times; and the benchmark's SPInProp step (one Adam
+    step through the reduced network) against the oracle's Adam step."""
     net, bt = synth.workload_cdr_single()
     bt = as_f32_batch(bt)
     rows, Xis, _ = eim_for(net, bt.s[0], 16)
     fnet = lrnr64.make_fast(net, rows, Xis)
     model, db = make(P, net, bt)
     install_fast(P, model, rows, Xis)
+    tol = {"fp32": TOL_FP32, "bf16x3": 1e-5, "tf32": 2.5e-3, "bf16": 2e-2}
+    oracle = {}
     for form, ref in (("fast", fnet), ("full", net)):
-        lo, ds, dbb = P.lrnr_residual_grad(model, form, "fp32", db)
-        ro, rs, rb = lrnr64.residual_grad(ref, bt, form)
-        assert rel(lo.cpu(), ro) < TOL_FP32, form
-        assert rel(ds.cpu(), rs) < TOL_FP32, form
-        assert rel(dbb.cpu(), rb) < TOL_FP32, form
+        ro, rs, rb = oracle[form] = lrnr64.residual_grad(ref, bt, form)
+        for prec in ("fp32", "bf16x3", "tf32", "bf16"):
+            lo, ds, dbb = P.lrnr_residual_grad(model, form, prec, db)
+            assert rel(lo.cpu(), ro) < tol[prec], (form, prec)
+            assert rel(ds.cpu(), rs) < tol[prec], (form, prec, rel(ds.cpu(), rs))
+            assert rel(dbb.cpu(), rb) < tol[prec], (form, prec, rel(dbb.cpu(), rb))
+    # one Adam step (bias-corrected, step 1): coordinate k moves by lr g_k / (|g_k| + eps);
+    # the smallest |g_k| here is 4e-6 of ||g|| (1.7e-7), where the FP32 gradient error
+    # (about 3e-7 ||g||) changes the move by up to 4e-3 lr: tolerance 1e-2 lr
+    s = torch.tensor(bt.s, dtype=torch.float32, device="cuda")
+    m, v = torch.zeros_like(s), torch.zeros_like(s)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lo = torch.zeros(1, dtype=torch.float32, device="cuda")
+    P.spinprop_step(model, "fast", "fp32", db, s, m, v, step, 1, lr=1e-3, loss_out=lo)
+    sr, _, _ = adam64.adam_step(bt.s[0], np.zeros_like(bt.s[0]), np.zeros_like(bt.s[0]), 1,
+                                oracle["fast"][1][0], lr=1e-3)
+    disp = np.abs(sr - bt.s[0]).max()
+    assert np.max(np.abs(s[0].cpu().numpy() - sr)) <= 1e-2 * disp
+    assert abs(lo.item() - oracle["fast"][0][0]) <= 1e-5 * abs(oracle["fast"][0][0])
     assert P.lrnr_last_device_status(model) == 0
