@@ -299,19 +299,29 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
     loop, FastLRNR FP32; plus the fast-phase loop against the same loop on the
     full-width FP32 LRNR (200 Adam steps on 16 instances)."""
     out = {}
-    # 512 instances, ~7.9 M points, one residual + gradient pass
+    # 512 instances, ~7.9 M points, one residual + gradient pass: the tile shape picked
+    # by the autotuner, the call replayed from a captured CUDA graph
+    from paper_2410_04001_gb300.autotune import autotune
     net, bt = synth.workload_batched()
     model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
     mats = select_rows_on_device(P, model, net, bt.s[0], dev, torch, synth)
     db = P.DeviceBatch.from_host(bt, dev)
+    tuned = autotune(model, db, "fast", "fp32", cache=None, reps=3)
     res = P.lrnr_residual_grad(model, "fast", "fp32", db)
     P.lrnr_timing(model, True)
-    ts_, km, kn = timed_steps(lambda: P.lrnr_residual_grad(model, "fast", "fp32", db, out=res), 10, model)
+    _, km, kn = timed_steps(lambda: P.lrnr_residual_grad(model, "fast", "fp32", db, out=res), 5, model)
     P.lrnr_timing(model, False)
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr, capture_error_mode="relaxed"):
+        P.lrnr_residual_grad(model, "fast", "fp32", db, out=res)
+    gr.replay()
+    ts_, _, _ = timed_steps(gr.replay, 10)
     ms = sum(ts_) / len(ts_)
     r = {"workload": "512 CDR instances, counts log-uniform [1,024, 65,536], M=256 r=16 L=5 rhat=16",
          "points": db.n_points, "points_per_s": db.n_points / (ms * 1e-3), "ms_per_call": ms,
-         "kernel_ms": km / max(1, kn)}
+         "kernel_ms": km / max(1, kn), "cuda_graph": True,
+         "autotuned_shape": {"nt": tuned["nt"], "ctas_per_sm": tuned["ctas_per_sm"]}}
     if with_oracle:
         from oracle import eim64, lrnr64
         rows, Xis = [], []
