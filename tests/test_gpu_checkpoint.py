@@ -17,7 +17,8 @@ def P():
     return P
 
 
-def test_resume_from_checkpoint_is_bit_identical(P, tmp_path):
+@pytest.mark.parametrize("method", ["eim", "deim"])
+def test_resume_from_checkpoint_is_bit_identical(P, tmp_path, method):
     from paper_2410_04001_gb300 import checkpoint
     g = synth.rng(91)
     net = synth.make_net(g, L=3, M=64, r=16)
@@ -33,7 +34,10 @@ def test_resume_from_checkpoint_is_bit_identical(P, tmp_path):
     s0 = torch.tensor(bt.s[:1], device=dev)
     for l in range(net.L):
         S = P.lrnr_snapshots(model, l, torch.tensor(xs, device=dev), torch.tensor(ts, device=dev), s0)
-        r, X, _ = P.fastlrnr_select_rows(model, l, S, 12)
+        if method == "eim":
+            r, X, _ = P.fastlrnr_select_rows(model, l, S, 12)
+        else:   # POD basis + DEIM rows: a general (not triangular) P^T Xi
+            r, X, _, _ = P.fastlrnr_select_rows_deim(model, l, S, 12, tol=1e-12)
         rows.append(r)
         Xis.append(X)
     db = P.DeviceBatch.from_host(bt)

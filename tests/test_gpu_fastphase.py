@@ -5,8 +5,9 @@ perturbations for several coefficient draws, then Adam steps of the l1 fast loss
 plus the l1 locality term through the reduced network (SPInProp), then the
 solution on the full-width network with the trained coefficients.
 
-Against the FP64 oracle: EIM rows bit-exact on the same snapshot matrices; every
-Adam step from the same state; the full-width solution at the trained
+Against the FP64 oracle: the device snapshots against the oracle's exact-LRNR
+states, the device EIM rows against the oracle's greedy on the oracle's snapshots;
+every Adam step from the same state; the full-width solution at the trained
 coefficients."""
 import numpy as np
 import pytest
@@ -45,7 +46,9 @@ def test_fast_phase_on_the_paper_convection_shape(P):
     rows, Xis = [], []
     for l in range(net.L):
         S = P.lrnr_snapshots(model, l, xs_d, ts_d, sd_d).cpu().numpy().T
-        p, Xi, used = eim64.eim_greedy(S, 5)
+        So = np.concatenate([lrnr64.hidden_states(net, d, xs, ts, l) for d in draws], axis=1)
+        assert np.max(np.abs(S - So)) < 1e-12
+        p, Xi, used = eim64.eim_greedy(So, 5)
         assert got[l][1] == used == 5
         assert np.array_equal(got[l][0].cpu().numpy(), p), l
         rows.append(p)
