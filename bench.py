@@ -294,9 +294,13 @@ def select_rows_on_device(P, model, net, s0, dev, torch, synth):
     return rows
 
 
-def oracle_fast_net(net, s0, synth):
-    """The oracle's own FastLRNR for the same construction: its exact-LRNR snapshots at
-    the same design, its greedy EIM."""
+def oracle_fast_net(P, model, net, s0, synth, torch, dev):
+    """The oracle's own FastLRNR for the same construction (its exact-LRNR snapshots at
+    the same design, its greedy EIM), installed on the device model as well, so that
+    the kernels' errors are measured on one reduced network.  (The device's own
+    selection, from its own snapshots, can differ at the deep layers, whose snapshot
+    spectra fall below rounding after about ten modes.)  Returns the oracle network
+    and its rows."""
     from oracle import eim64, lrnr64
     xs, ts = synth.snapshot_design(synth.rng(77), 8)
     rows, Xis = [], []
@@ -304,6 +308,9 @@ def oracle_fast_net(net, s0, synth):
         p, Xi, _ = eim64.eim_greedy(lrnr64.hidden_states(net, s0, xs, ts, l), 16)
         rows.append(p)
         Xis.append(Xi)
+        P.fastlrnr_select_rows(model, l, None, len(p),
+                               rows_in=torch.tensor(p.astype("int32"), device=dev),
+                               Xi_in=torch.tensor(Xi.T.copy(), device=dev))
     return lrnr64.make_fast(net, rows, Xis), rows
 
 
@@ -337,8 +344,9 @@ def config_variants(P, synth, np, torch, dev, timed_steps, peak, with_oracle):
          "autotuned_shape": {"nt": tuned["nt"], "ctas_per_sm": tuned["ctas_per_sm"]}}
     if with_oracle:
         from oracle import lrnr64
-        fnet, rows_o = oracle_fast_net(net, bt.s[0], synth)
+        fnet, rows_o = oracle_fast_net(P, model, net, bt.s[0], synth, torch, dev)
         r["eim_rows_match_oracle"] = all(np.array_equal(a, b) for a, b in zip(rows_o, rows_dev))
+        res = P.lrnr_residual_grad(model, "fast", "fp32", db)
         f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
         errs = []
         for i in (0, 255, 511):
@@ -782,7 +790,7 @@ def main():
                            x_int=f32(bt.x_int), t_int=f32(bt.t_int), x_ic=f32(bt.x_ic), t_bc=f32(bt.t_bc))
         # the oracle's own construction (its snapshots, its greedy); the device's rows
         # are compared with it, not fed to it
-        fnet, rows_o = oracle_fast_net(net, bt.s[0], synth)
+        fnet, rows_o = oracle_fast_net(P, model, net, bt.s[0], synth, torch, dev)
         for form, ref, precs in (("fast", fnet, ("fp32", "bf16", "tf32", "bf16x3")),
                                  ("full", net, ("fp32", "bf16", "tf32", "bf16x3"))):
             ro, rs, rb = lrnr64.residual_grad(ref, bt32, form)

@@ -15,7 +15,7 @@ import torch
 
 import synth
 from oracle import adam64, eim64, lrnr64
-from tests.gpu_common import TOL_FP32, as_f32_batch, as_f32_net, rel
+from tests.gpu_common import TOL_FP32, as_f32_batch, as_f32_net, install_fast, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +54,9 @@ def test_fast_phase_on_the_paper_convection_shape(P):
         rows.append(p)
         Xis.append(Xi)
     fnet = lrnr64.make_fast(net, rows, Xis)
+    # the steps below compare the same reduced network: the oracle's rows and bases
+    # installed on the device (its own bases differ from them at rounding level)
+    install_fast(P, model, rows, Xis)
 
     # Adam steps of the fast loss + locality, one at a time from the device state
     dX = P.DeviceBatch.from_host(bx)
