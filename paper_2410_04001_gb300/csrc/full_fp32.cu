@@ -32,53 +32,73 @@ __host__ __device__ inline size_t full_store_floats(int L, int RM, int NT) {
   return (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * NT;
 }
 
-template <int RM, int NI>
-__device__ __forceinline__ void load_row(const float *__restrict__ W, float (&w)[RM]) {
-  if constexpr (NI % 4 == 0) {
+// Rank-r jets are held as RM/2 pairs per channel so that the products run on the
+// packed FP32 FMA (two lanes of arithmetic per instruction).
+__device__ __forceinline__ float2 ff2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fm2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Row W[0..N) as pairs (N a multiple of 4, or 2, or 1; nothing past N is read).
+template <int RM, int N>
+__device__ __forceinline__ void load_row2(const float *__restrict__ W, float2 (&w)[RM / 2]) {
+  if constexpr (N % 4 == 0) {
 #pragma unroll
-    for (int k = 0; k < NI; k += 4) {
+    for (int k = 0; k < N; k += 4) {
       const float4 v = __ldg(reinterpret_cast<const float4 *>(W + k));
-      w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+      w[k / 2] = make_float2(v.x, v.y);
+      w[k / 2 + 1] = make_float2(v.z, v.w);
     }
+  } else if constexpr (N == 2) {
+    w[0] = __ldg(reinterpret_cast<const float2 *>(W));
   } else {
-#pragma unroll
-    for (int k = 0; k < NI; ++k) w[k] = __ldg(W + k);
+    w[0] = make_float2(__ldg(W), 0.0f);
   }
 }
 
-// One hidden layer forward: q (input jet, overwritten with s * q) -> qn.
+// One hidden layer forward: y = s * q (input jet) -> qn (next rank-r input).  Per row
+// the pre-activation is an even/odd pair of partial dot products added at the end.
 template <int RM, int NI, int NO, int C>
 __device__ __forceinline__ void layer_fwd(const float *__restrict__ U, const float *__restrict__ b,
                                           const float *__restrict__ Vn, int M,
-                                          const float (&y)[C][RM], float (&qn)[C][RM]) {
+                                          const float2 (&y)[C][RM / 2], float2 (&qn)[C][RM / 2]) {
+  static_assert(NI % 2 == 0, "input rank is padded to pairs");
 #pragma unroll 2
   for (int i = 0; i < M; ++i) {
-    float uw[RM], vw[RM];
-    load_row<RM, NI>(U + (int64_t)i * RM, uw);
-    load_row<RM, NO>(Vn + (int64_t)i * RM, vw);
+    float2 uw[RM / 2], vw[RM / 2];
+    load_row2<RM, NI>(U + (int64_t)i * RM, uw);
+    load_row2<RM, NO>(Vn + (int64_t)i * RM, vw);
+    float2 acc[C];
+    acc[0] = make_float2(__ldg(b + i), 0.0f);
+#pragma unroll
+    for (int c = 1; c < C; ++c) acc[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int kk = 0; kk < NI / 2; ++kk)
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = ff2(uw[kk], y[c][kk], acc[c]);
     float a[C][1];
-    a[0][0] = __ldg(b + i);
 #pragma unroll
-    for (int c = 1; c < C; ++c) a[c][0] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < NI; ++k)
-#pragma unroll
-      for (int c = 0; c < C; ++c) a[c][0] = fmaf(uw[k], y[c][k], a[c][0]);
+    for (int c = 0; c < C; ++c) a[c][0] = acc[c].x + acc[c].y;
     act_fwd<C, 1>(a);
+    if constexpr (NO == 1) {
 #pragma unroll
-    for (int j = 0; j < NO; ++j)
+      for (int c = 0; c < C; ++c) qn[c][0].x = fmaf(vw[0].x, a[c][0], qn[c][0].x);
+    } else {
 #pragma unroll
-      for (int c = 0; c < C; ++c) qn[c][j] = fmaf(vw[j], a[c][0], qn[c][j]);
+      for (int jj = 0; jj < NO / 2; ++jj)
+#pragma unroll
+        for (int c = 0; c < C; ++c) qn[c][jj] = ff2(vw[jj], make_float2(a[c][0], a[c][0]), qn[c][jj]);
+    }
   }
 }
 
 // One hidden layer reverse: given y = s * q (input), qb (adjoint of the output
-// rank-r vector), accumulate pb = U^T abar and the bias gradient rows into red_w.
+// rank-r vector), accumulate pb = U^T abar and the bias gradient rows into red_db.
 template <int RM, int NI, int NO, int C>
 __device__ __forceinline__ void layer_bwd(const float *__restrict__ U, const float *__restrict__ b,
                                           const float *__restrict__ Vn, int M,
-                                          const float (&y)[C][RM], const float (&qb)[C][RM],
-                                          float (&pb)[C][RM], float *red_db) {
+                                          const float2 (&y)[C][RM / 2],
+                                          const float2 (&qb)[C][RM / 2], float2 (&pb)[C][RM / 2],
+                                          float *red_db) {
+  static_assert(NI % 2 == 0, "input rank is padded to pairs");
   const int lane = threadIdx.x & 31;
   for (int i0 = 0; i0 < M; i0 += 8) {
     float ab0[8];
@@ -87,28 +107,39 @@ __device__ __forceinline__ void layer_bwd(const float *__restrict__ U, const flo
       const int i = i0 + ii;
       ab0[ii] = 0.0f;
       if (i < M) {
-        float uw[RM], vw[RM];
-        load_row<RM, NI>(U + (int64_t)i * RM, uw);
-        load_row<RM, NO>(Vn + (int64_t)i * RM, vw);
+        float2 uw[RM / 2], vw[RM / 2];
+        load_row2<RM, NI>(U + (int64_t)i * RM, uw);
+        load_row2<RM, NO>(Vn + (int64_t)i * RM, vw);
+        float2 acc[C], accw[C];
+        acc[0] = make_float2(__ldg(b + i), 0.0f);
+#pragma unroll
+        for (int c = 1; c < C; ++c) acc[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < C; ++c) accw[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int kk = 0; kk < NI / 2; ++kk)
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[c] = ff2(uw[kk], y[c][kk], acc[c]);
         float a[C][1], wb[C][1];
-        a[0][0] = __ldg(b + i);
+        if constexpr (NO == 1) {
 #pragma unroll
-        for (int c = 1; c < C; ++c) a[c][0] = 0.0f;
+          for (int c = 0; c < C; ++c) wb[c][0] = vw[0].x * qb[c][0].x;
+        } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) wb[c][0] = 0.0f;
+          for (int jj = 0; jj < NO / 2; ++jj)
 #pragma unroll
-        for (int k = 0; k < NI; ++k)
+            for (int c = 0; c < C; ++c) accw[c] = ff2(vw[jj], qb[c][jj], accw[c]);
 #pragma unroll
-          for (int c = 0; c < C; ++c) a[c][0] = fmaf(uw[k], y[c][k], a[c][0]);
+          for (int c = 0; c < C; ++c) wb[c][0] = accw[c].x + accw[c].y;
+        }
 #pragma unroll
-        for (int j = 0; j < NO; ++j)
-#pragma unroll
-          for (int c = 0; c < C; ++c) wb[c][0] = fmaf(vw[j], qb[c][j], wb[c][0]);
+        for (int c = 0; c < C; ++c) a[c][0] = acc[c].x + acc[c].y;
         act_bwd<C, 1>(a, wb);
 #pragma unroll
-        for (int k = 0; k < NI; ++k)
+        for (int kk = 0; kk < NI / 2; ++kk)
 #pragma unroll
-          for (int c = 0; c < C; ++c) pb[c][k] = fmaf(uw[k], wb[c][0], pb[c][k]);
+          for (int c = 0; c < C; ++c)
+            pb[c][kk] = ff2(uw[kk], make_float2(wb[c][0], wb[c][0]), pb[c][kk]);
         ab0[ii] = wb[0][0];
       }
     }
@@ -120,6 +151,7 @@ __device__ __forceinline__ void layer_bwd(const float *__restrict__ U, const flo
 template <int RM, int NT, int C>
 __device__ void full_tile(const KParams &p, const Tile &T, const float *__restrict__ s_s,
                           float *__restrict__ q_s, float *red_w) {
+  constexpr int RP = RM / 2;
   const int tid = threadIdx.x;
   const int L = p.L, M = p.M;
   const int64_t LS = full_layer_floats(M, RM);
@@ -131,19 +163,22 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
   const float x = pt.x, t = pt.t;
   float v00 = __ldg(V0 + 0), v01 = __ldg(V0 + 1), v10 = __ldg(V0 + R1), v11 = __ldg(V0 + R1 + 1);
 
-  float q[C][RM];
+  float2 q[C][RP];
   auto input_jet = [&]() {
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int k = 0; k < RM; ++k) q[c][k] = 0.0f;
-    q[0][0] = v00 * x + v10 * t;
-    q[0][1] = v01 * x + v11 * t;
+      for (int kk = 0; kk < RP; ++kk) q[c][kk] = make_float2(0.0f, 0.0f);
+    q[0][0] = make_float2(v00 * x + v10 * t, v01 * x + v11 * t);
     if constexpr (C >= 3) {
-      q[1][0] = v10; q[1][1] = v11;
-      q[2][0] = v00; q[2][1] = v01;
+      q[1][0] = make_float2(v10, v11);
+      q[2][0] = make_float2(v00, v01);
     }
   };
+  auto s_pair = [&](int l, int kk) {
+    return make_float2(s_s[l * RM + 2 * kk], s_s[l * RM + 2 * kk + 1]);
+  };
+  auto slot = [&](int l, int c, int k) { return (((l - 1) * 4 + c) * RM + k) * NT + tid; };
   input_jet();
 
   for (int l = 0; l < L; ++l) {
@@ -154,13 +189,19 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < RM; ++k) q_s[(((l - 1) * 4 + c) * RM + k) * NT + tid] = q[c][k];
+        for (int kk = 0; kk < RP; ++kk) {
+          q_s[slot(l, c, 2 * kk)] = q[c][kk].x;
+          q_s[slot(l, c, 2 * kk + 1)] = q[c][kk].y;
+        }
     }
-    float y[C][RM];
+    float2 y[C][RP];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int k = 0; k < RM; ++k) { y[c][k] = q[c][k] * s_s[l * RM + k]; q[c][k] = 0.0f; }
+      for (int kk = 0; kk < RP; ++kk) {
+        y[c][kk] = fm2(q[c][kk], s_pair(l, kk));
+        q[c][kk] = make_float2(0.0f, 0.0f);
+      }
     if (l == 0 && l == L - 1) layer_fwd<RM, R1, 1, C>(U, b, Vn, M, y, q);
     else if (l == 0) layer_fwd<RM, R1, RM, C>(U, b, Vn, M, y, q);
     else if (l == L - 1) layer_fwd<RM, RM, 1, C>(U, b, Vn, M, y, q);
@@ -169,7 +210,7 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
   const float sL = s_s[L * RM];
   float u[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-  for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0];
+  for (int c = 0; c < C; ++c) u[c] = Uout * sL * q[c][0].x;
   u[0] += bout;
 
   float ub[4], lp;
@@ -180,16 +221,16 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
     const float ls = warp_sum(lp);
     if ((tid & 31) == 0) red_w[0] += ls;
   }
-  float qb[C][RM];
+  float2 qb[C][RP];
   {
     float dsL = 0.0f;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const float pbv = Uout * ub[c];
-      dsL += pbv * q[c][0];
+      dsL += pbv * q[c][0].x;
 #pragma unroll
-      for (int k = 0; k < RM; ++k) qb[c][k] = 0.0f;
-      qb[c][0] = sL * pbv;
+      for (int kk = 0; kk < RP; ++kk) qb[c][kk] = make_float2(0.0f, 0.0f);
+      qb[c][0].x = sL * pbv;
     }
     const float s0 = warp_sum(dsL);
     const float s1 = warp_sum(ub[0]);
@@ -206,15 +247,19 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < RM; ++k) q[c][k] = q_s[(((l - 1) * 4 + c) * RM + k) * NT + tid];
+        for (int kk = 0; kk < RP; ++kk)
+          q[c][kk] = make_float2(q_s[slot(l, c, 2 * kk)], q_s[slot(l, c, 2 * kk + 1)]);
     } else {
       input_jet();
     }
-    float y[C][RM], pb[C][RM];
+    float2 y[C][RP], pb[C][RP];
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int k = 0; k < RM; ++k) { y[c][k] = q[c][k] * s_s[l * RM + k]; pb[c][k] = 0.0f; }
+      for (int kk = 0; kk < RP; ++kk) {
+        y[c][kk] = fm2(q[c][kk], s_pair(l, kk));
+        pb[c][kk] = make_float2(0.0f, 0.0f);
+      }
     float *red_db = red_w + DB0 + l * M;
     if (l == 0 && l == L - 1) layer_bwd<RM, R1, 1, C>(U, b, Vn, M, y, qb, pb, red_db);
     else if (l == 0) layer_bwd<RM, R1, RM, C>(U, b, Vn, M, y, qb, pb, red_db);
@@ -222,18 +267,19 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
     else layer_bwd<RM, RM, RM, C>(U, b, Vn, M, y, qb, pb, red_db);
     float g[RM];
 #pragma unroll
-    for (int k = 0; k < RM; ++k) {
-      float d = 0.0f;
+    for (int kk = 0; kk < RP; ++kk) {
+      float2 d = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int c = 0; c < C; ++c) d = fmaf(pb[c][k], q[c][k], d);
-      g[k] = d;
+      for (int c = 0; c < C; ++c) d = ff2(pb[c][kk], q[c][kk], d);
+      g[2 * kk] = d.x;
+      g[2 * kk + 1] = d.y;
     }
     warp_accumulate<RM>(g, red_w, [&](int j) { return 1 + l * RM + j; });
     if (l > 0) {
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int k = 0; k < RM; ++k) qb[c][k] = pb[c][k] * s_s[l * RM + k];
+        for (int kk = 0; kk < RP; ++kk) qb[c][kk] = fm2(pb[c][kk], s_pair(l, kk));
     }
   }
 }
