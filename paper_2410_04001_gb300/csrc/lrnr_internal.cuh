@@ -268,9 +268,8 @@ cudaError_t launch_reduce(const KParams &p, int nb_needed, int form_fast, const 
                           int rows_stride, float *loss_out, float *dL_ds, float *dL_db,
                           int sum_m, int num_sms, cudaStream_t st);
 // Batches of a few instances (at most 2 * num_sms / 8) reduce with one 8-CTA
-// cluster per instance; otherwise gsum (n_inst x groups x entries floats) and cnt
-// (n_inst zeroed ints) select the two-level reduction, and with nullptr the
-// one-block-per-instance kernel runs.
+// cluster per instance; otherwise the two-level reduction runs on gsum (n_inst x
+// groups x entries floats) and cnt (n_inst zeroed ints), which must then be given.
 cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, const int64_t *step,
                                float lr, float b1, float b2, float eps, float lam,
                                const float *anchor, float *loss_out, float *gsum, int *cnt,

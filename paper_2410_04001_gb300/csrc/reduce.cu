@@ -116,67 +116,6 @@ struct AdamArgs {
   const float *anchor;
 };
 
-// One block per instance: reduce loss and dL/ds, add the locality subgradient,
-// then apply Adam to the instance's s.
-__global__ void __launch_bounds__(1024) k_reduce_adam(const __grid_constant__ AdamArgs A) {
-  const RedArgs &a = A.red;
-  __shared__ float sh[32][33];
-  __shared__ float gsh[(LMAX + 1) * RMAX];
-  __shared__ float lsum[32];
-  const int i = blockIdx.x;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
-  const int DB0 = 1 + (a.L + 1) * a.RM;
-  float loss = 0.0f;
-  for (int c0 = 0; c0 < DB0; c0 += 32) {
-    const int j = c0 + tx;
-    float acc = 0.0f;
-    if (j < DB0)
-      acc = column_sum(a.partial, a.P, j, t0, t1, ty);
-    sh[ty][tx] = acc;
-    __syncthreads();
-    if (ty == 0 && j < DB0) {
-      float tot = 0.0f;
-#pragma unroll
-      for (int g = 0; g < 32; ++g) tot += sh[g][tx];
-      if (j == 0) loss = tot;
-      else {
-        const int l = (j - 1) / a.RM, k = (j - 1) % a.RM;
-        if (k < a.r[l]) gsh[a.roff[l] + k] = tot;
-      }
-    }
-    __syncthreads();
-  }
-  const int64_t k = *A.step;
-  const float bc1 = 1.0f - powf(A.b1, (float)k);
-  const float bc2 = 1.0f - powf(A.b2, (float)k);
-  float loc = 0.0f;
-  for (int q = tid; q < a.sum_r; q += 1024) {
-    const int64_t o = (int64_t)i * a.sum_r + q;
-    const float sv = A.s[o];
-    float g = gsh[q];
-    if (A.anchor) {
-      const float d = sv - A.anchor[o];
-      loc += A.lam * fabsf(d);
-      g += A.lam * (float)((d > 0.0f) - (d < 0.0f));
-    }
-    if (a.dL_ds) a.dL_ds[o] = g;
-    const float mv = A.b1 * A.m[o] + (1.0f - A.b1) * g;
-    const float vv = A.b2 * A.v[o] + (1.0f - A.b2) * g * g;
-    A.m[o] = mv;
-    A.v[o] = vv;
-    A.s[o] = sv - A.lr * (mv / bc1) / (sqrtf(vv / bc2) + A.eps);
-  }
-  loc = warp_sum(loc);
-  if (tx == 0) lsum[ty] = loc;
-  __syncthreads();
-  if (tid == 0) {
-    float lt = 0.0f;
-    for (int w = 0; w < 32; ++w) lt += lsum[w];
-    if (a.loss_out) a.loss_out[i] = loss + lt;
-  }
-}
-
 // Two-level version for the SPInProp step: block (i, g) sums the partial rows
 // t = t0 + g, t0 + g + TG, ... of instance i for every entry and writes one group
 // row; the last block of instance i to finish (atomic ticket) adds the TG group
@@ -480,7 +419,7 @@ cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, c
   } else if (gsum && cnt) {
     k_reduce_adam2<<<dim3(p.n_inst, kAdamGroups), 256, 0, st>>>(A, gsum, cnt);
   } else {
-    k_reduce_adam<<<p.n_inst, dim3(32, 32), 0, st>>>(A);
+    return cudaErrorInvalidValue;   // the two-level form needs its group rows and tickets
   }
   return cudaGetLastError();
 }
