@@ -239,10 +239,9 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
       red_w[DB0 + L * M] += s1;
     }
   }
-  for (int l = L - 1; l >= 0; --l) {
-    const float *U = p.pack + l * LS;
-    const float *b = U + (int64_t)M * RM;
-    const float *Vn = b + pad4(M);
+  // the layer's input jet q is read from the store twice (for s * q before the
+  // layer, for dL/ds after it) instead of being held through the layer
+  auto load_q = [&](int l) {
     if (l > 0) {
 #pragma unroll
       for (int c = 0; c < C; ++c)
@@ -252,6 +251,12 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
     } else {
       input_jet();
     }
+  };
+  for (int l = L - 1; l >= 0; --l) {
+    const float *U = p.pack + l * LS;
+    const float *b = U + (int64_t)M * RM;
+    const float *Vn = b + pad4(M);
+    load_q(l);
     float2 y[C][RP], pb[C][RP];
 #pragma unroll
     for (int c = 0; c < C; ++c)
@@ -265,6 +270,7 @@ __device__ void full_tile(const KParams &p, const Tile &T, const float *__restri
     else if (l == 0) layer_bwd<RM, R1, RM, C>(U, b, Vn, M, y, qb, pb, red_db);
     else if (l == L - 1) layer_bwd<RM, RM, 1, C>(U, b, Vn, M, y, qb, pb, red_db);
     else layer_bwd<RM, RM, RM, C>(U, b, Vn, M, y, qb, pb, red_db);
+    load_q(l);
     float g[RM];
 #pragma unroll
     for (int kk = 0; kk < RP; ++kk) {
