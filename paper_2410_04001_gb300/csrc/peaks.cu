@@ -1,6 +1,7 @@
 // Compute-throughput microbenchmarks for the roofline denominators of the SIMT
 // kernels: FP32 fused multiply-add (scalar and packed two-lane), the MUFU tanh
-// approximation, the accurate tanhf the FP32 kernels call, and FP64 FMA; plus the
+// approximation, the CUDA library's accurate tanhf (the FP32 kernels form tanh from
+// ex2 and rcp instead, two MUFU operations), and FP64 FMA; plus the
 // SM clock seen while they run.  Each kernel runs many independent chains per
 // thread on a grid of 4 CTAs of 256 threads per SM, so that issue, not latency,
 // limits it.
