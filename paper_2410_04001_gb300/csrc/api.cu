@@ -46,6 +46,7 @@ struct lrnr_model {
   void *ftc_pack = nullptr;                    // tensor-core pack of the reduced network
   void *tf_pack = nullptr;                     // the same two packs in TF32
   void *ftf_pack = nullptr;
+  float *fastk_pack = nullptr;                 // FP32 reduced pack for ranks 32 / 64 (fastk.cu)
   int ftc_nc = 16;                             // its chunk width (32 at rank 64)
   // reduced layers (host, FP64): Uh [rh][r_l], bh [rh], Vh [rh][r_{l+1}], rows [rh]
   int rhat[LMAX] = {0};
@@ -196,12 +197,18 @@ lrnr_status build_fast_pack(lrnr_model *m) {
   tail[2 * R1] = (float)m->U[L][0];
   tail[2 * R1 + 1] = (float)m->b[L][0];
   if (m->fast_pack) cudaFree(m->fast_pack);
+  if (m->fastk_pack) cudaFree(m->fastk_pack);
   if (m->rows_dev) cudaFree(m->rows_dev);
   m->fast_pack = nullptr;
+  m->fastk_pack = nullptr;
   m->rows_dev = nullptr;
   if (fp32_ok) {
     CK(cudaMalloc(&m->fast_pack, pk.size() * sizeof(float)));
     CK(cudaMemcpy(m->fast_pack, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
+  } else if ((RMp == 32 || RMp == 64) && RHp <= 16) {
+    // ranks above the rank-r jet kernel: the same pack for the reduced-coordinate kernel
+    CK(cudaMalloc(&m->fastk_pack, pk.size() * sizeof(float)));
+    CK(cudaMemcpy(m->fastk_pack, pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   CK(cudaMalloc(&m->rows_dev, rw.size() * sizeof(int32_t)));
   CK(cudaMemcpy(m->rows_dev, rw.data(), rw.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -301,15 +308,24 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     if (prec != LRNR_FP32) return LRNR_ENOTSUP;
     rc = build_fast_pack(m);
     if (rc != LRNR_OK) return rc;
-    if (!m->fast_pack) return LRNR_ENOTSUP;   // ranks above the FP32 instantiations
     p.RM = m->fRM;
     p.RH = m->fRH;
-    p.pack = m->fast_pack;
     for (int l = 0; l < m->L; ++l) p.rh[l] = m->rhat[l];
-    p.fused_tiles = bt->n_inst <= 4096 ? 1 : 0;   // the kernel computes its tile offsets
-    p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
-    if (!p.nt) return LRNR_ENOTSUP;
-    {
+    if (!m->fast_pack) {
+      // ranks above the rank-r jet kernel (padded 32 / 64): the reduced-coordinate
+      // kernel, when the reduced width allows it
+      if (!m->fastk_pack ||
+          !fastk_supported(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1)))
+        return LRNR_ENOTSUP;
+      p.fastk = 1;
+      p.pack = m->fastk_pack;
+      p.fused_tiles = 0;
+      p.nt = fastk_nt();
+    } else {
+      p.pack = m->fast_pack;
+      p.fused_tiles = bt->n_inst <= 4096 ? 1 : 0;   // the kernel computes its tile offsets
+      p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
+      if (!p.nt) return LRNR_ENOTSUP;
       const int tn = m->tune_nt[LRNR_FAST][prec];
       if (tn && fast_smem_bytes(m->L, p.RM, p.RH, tn, partial_len(m->L, p.RM, m->L * p.RH + 1)) <=
                     (size_t)kSmemBudget)
@@ -361,7 +377,10 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     int per_sm = fast_ctas_per_sm(p);
     if (m->tune_cta[LRNR_FAST][prec] > 0) per_sm = std::min(per_sm, m->tune_cta[LRNR_FAST][prec]);
     ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
-    if (grad) scr_bytes = fast_scratch_floats(m->L, p.RM, p.RH, p.nt, ps.grid_cap) * sizeof(float);
+    if (grad)
+      scr_bytes = (p.fastk ? fastk_scratch_floats(m->L, p.RH, ps.grid_cap)
+                           : fast_scratch_floats(m->L, p.RM, p.RH, p.nt, ps.grid_cap)) *
+                  sizeof(float);
   } else {
     // the FP32 full-width kernel also keeps layer inputs in a per-CTA scratch
     int per_sm = full_fp32_ctas_per_sm(p);
@@ -371,8 +390,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   }
   // Batches whose tiles fit in one round of the FastLRNR grid (2 CTAs per SM) are
   // reduced inside the kernel (group rows + tickets): one launch instead of two.
-  const bool fused_red =
-      grad && form == LRNR_FAST && prec == LRNR_FP32 && tiles <= 2 * (int64_t)m->num_sms;
+  const bool fused_red = grad && form == LRNR_FAST && prec == LRNR_FP32 && !p.fastk &&
+                         tiles <= 2 * (int64_t)m->num_sms;
   if (fused_red) {
     p.fast_regs = 2;
     ps.grid_cap = (int)std::min<int64_t>(tiles, 2 * (int64_t)m->num_sms);
@@ -955,6 +974,7 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->tf_pack);
   cudaFree(m->ftf_pack);
   cudaFree(m->fast_pack);
+  cudaFree(m->fastk_pack);
   cudaFree(m->rows_dev);
   cudaFree(m->status_dev);
   cudaFree(m->ws);

@@ -29,6 +29,7 @@ size_t fast_scratch_floats(int L, int RM, int RH, int NT, int grid) {
 }
 
 int fast_ctas_per_sm(const KParams &p) {
+  if (p.fastk) return fastk_ctas_per_sm(p);
   if (p.RM == 8 && p.RH == 8) return fast_ctas_per_sm_t<8, 8>(p);
   if (p.RM == 16 && p.RH == 8) return fast_ctas_per_sm_t<16, 8>(p);
   if (p.RM == 8 && p.RH == 16) return fast_ctas_per_sm_t<8, 16>(p);
@@ -37,6 +38,7 @@ int fast_ctas_per_sm(const KParams &p) {
 }
 
 cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st) {
+  if (p.fastk) return launch_fastk(p, grid, st);
   if (p.nt != 128 && p.nt != 64 && p.nt != 32) return cudaErrorInvalidValue;
   if (!p.scratch && p.grad) return cudaErrorInvalidValue;
   if (p.RM == 8 && p.RH == 8) return launch_fast_t<8, 8>(p, grid, st);

@@ -56,6 +56,7 @@ struct KParams {
   float *scratch;              // per-CTA store of layer inputs (FP32 and tensor-core kernels)
   int fused_tiles;             // the tile kernel computes the tile offsets itself
   int fast_regs;               // FastLRNR kernel build: 3 = 168 registers, else 255
+  int fastk;                   // FastLRNR in reduced coordinates (ranks 32 / 64, fastk.cu)
   uint32_t max_wait;           // iteration cap of every device-side wait
   // Fixed-order reduction inside the FastLRNR kernel (fused_red != 0; chosen for
   // batches whose tiles fit in one round of the grid, where a second launch would
@@ -257,6 +258,12 @@ cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_
 // grid_cap bounds the persistent grid (never more CTAs than tiles); the FastLRNR
 // kernel is launched with exactly `grid` CTAs (its scratch is sized for them).
 cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
+// FastLRNR FP32 in reduced coordinates for padded ranks 32 and 64 (RH 8 or 16).
+bool fastk_supported(int L, int RM, int RH, int P);
+int fastk_nt();
+size_t fastk_scratch_floats(int L, int RH, int grid);
+int fastk_ctas_per_sm(const KParams &p);
+cudaError_t launch_fastk(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st);
 // NC: 32-column chunks (full-width networks, one CTA per SM) or 16-column chunks
 // (narrow networks, two CTAs per SM while RM <= 32).
