@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(KT, 2) k_fastk(const __grid_constant__ KParams
   const int npack = fast_pack_floats(L, RM, RH);
   for (int i = tid; i < npack; i += KT) w_s[i] = __ldg(p.pack + i);
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
+  __syncthreads();   // the pack is read by every thread below
   const float *V0 = w_s + L * LS;
   const float Uout = V0[2 * R1];
   const int ntiles = __ldg(p.tile_off + p.n_inst);
