@@ -309,8 +309,14 @@ __global__ void __launch_bounds__(KT, 2) k_fastk(const __grid_constant__ KParams
           if (j < R1)
             for (int k = 0; k < R1; ++k) acc = fmaf(Uh[k] * sl[k], V0[j * R1 + k], acc);
         } else {
+          // four partial sums over the rank (RM is a multiple of 4)
           const float *Vp = w_s + (l - 1) * LS + RH * RM + RH + j * RM;
-          for (int k = 0; k < RM; ++k) acc = fmaf(Uh[k] * sl[k], Vp[k], acc);
+          float a4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+          for (int k = 0; k < RM; k += 4)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a4[q] = fmaf(Uh[k + q] * sl[k + q], Vp[k + q], a4[q]);
+          acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
         }
         K_s[e] = acc;
       } else {
@@ -328,32 +334,56 @@ __global__ void __launch_bounds__(KT, 2) k_fastk(const __grid_constant__ KParams
       fastk_tile<RM, RH, 1>(p, T, w_s, K_s, kout_s, G_w, q_g, a_g, red_w);
     if (p.grad) {
       __syncthreads();
-      // dL/ds from the tile's G (warps added in order), projected through the bases;
-      // written into warp 0's partial row, whose dL/ds entries are otherwise zero
+      // the warps' G added in order into warp 0's block
+      for (int e = tid; e < GW; e += KT) {
+        float g = G_s[e];
+#pragma unroll
+        for (int w = 1; w < KT / 32; ++w) g += G_s[w * GW + e];
+        G_s[e] = g;
+      }
+      __syncthreads();
+      // dL/ds from the tile's G, projected through the bases (two partial sums per
+      // entry); written into warp 0's partial row, whose dL/ds entries are otherwise zero
       for (int e = tid; e < (L + 1) * RM; e += KT) {
         const int l = e / RM, k = e % RM;
         if (k >= p.r[l]) continue;
-        float acc = 0.0f;
-        if (l < L) {
-          const float *Uh = w_s + l * LS;
-          const int nin = l == 0 ? R1 : RH;
-          for (int i = 0; i < RH; ++i)
-            for (int j = 0; j < nin; ++j) {
-              float g = 0.0f;
-              for (int w = 0; w < KT / 32; ++w) g += G_s[w * GW + l * RH * RH + i * RH + j];
-              const float vjk = l == 0 ? V0[j * R1 + k]
-                                       : w_s[(l - 1) * LS + RH * RM + RH + j * RM + k];
-              acc = fmaf(Uh[i * RM + k] * vjk, g, acc);
-            }
-        } else {
-          const float *Vp = w_s + (L - 1) * LS + RH * RM + RH;
-          for (int j = 0; j < RH; ++j) {
-            float g = 0.0f;
-            for (int w = 0; w < KT / 32; ++w) g += G_s[w * GW + L * RH * RH + j];
-            acc = fmaf(Uout * Vp[j * RM + k], g, acc);
+        float acc0 = 0.0f, acc1 = 0.0f;
+        if (l == 0) {
+          const float *Uh = w_s;
+#pragma unroll
+          for (int i = 0; i < RH; ++i) {
+            const float *Gi = G_s + i * RH;
+            const float ui = Uh[i * RM + k];
+            acc0 = fmaf(ui * V0[k], Gi[0], acc0);
+            acc1 = fmaf(ui * V0[R1 + k], Gi[1], acc1);
           }
+        } else if (l < L) {
+          const float *Uh = w_s + l * LS;
+          const float *Vp = w_s + (l - 1) * LS + RH * RM + RH + k;
+          const float *Gl = G_s + l * RH * RH;
+          for (int i = 0; i < RH; ++i) {
+            const float ui = Uh[i * RM + k];
+            float h0 = 0.0f, h1 = 0.0f;
+#pragma unroll
+            for (int j = 0; j < RH; j += 2) {
+              h0 = fmaf(Vp[j * RM], Gl[i * RH + j], h0);
+              h1 = fmaf(Vp[(j + 1) * RM], Gl[i * RH + j + 1], h1);
+            }
+            acc0 = fmaf(ui, h0, acc0);
+            acc1 = fmaf(ui, h1, acc1);
+          }
+        } else {
+          const float *Vp = w_s + (L - 1) * LS + RH * RM + RH + k;
+          const float *g = G_s + L * RH * RH;
+#pragma unroll
+          for (int j = 0; j < RH; j += 2) {
+            acc0 = fmaf(Vp[j * RM], g[j], acc0);
+            acc1 = fmaf(Vp[(j + 1) * RM], g[j + 1], acc1);
+          }
+          acc0 *= Uout;
+          acc1 *= Uout;
         }
-        red_s[1 + l * RM + k] += acc;
+        red_s[1 + l * RM + k] += acc0 + acc1;
       }
       __syncthreads();
       for (int j = tid; j < p.P; j += KT) {
