@@ -314,12 +314,13 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     if (!m->fast_pack) {
       // ranks above the rank-r jet kernel (padded 32 / 64): the reduced-coordinate
       // kernel, when the reduced width allows it
-      if (!m->fastk_pack ||
-          !fastk_supported(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1)))
-        return LRNR_ENOTSUP;
+      const int P = partial_len(m->L, p.RM, m->L * p.RH + 1);
+      if (!m->fastk_pack || !fastk_supported(m->L, p.RM, p.RH, P, 0)) return LRNR_ENOTSUP;
       p.fastk = 1;
       p.pack = m->fastk_pack;
-      p.fused_tiles = 0;
+      // the kernel computes its tile offsets when they fit in shared memory
+      p.fused_tiles =
+          bt->n_inst <= 4096 && fastk_supported(m->L, p.RM, p.RH, P, bt->n_inst) ? 1 : 0;
       p.nt = fastk_nt();
     } else {
       p.pack = m->fast_pack;
@@ -390,12 +391,14 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   }
   // Batches whose tiles fit in one round of the FastLRNR grid (2 CTAs per SM) are
   // reduced inside the kernel (group rows + tickets): one launch instead of two.
-  const bool fused_red = grad && form == LRNR_FAST && prec == LRNR_FP32 && !p.fastk &&
+  const bool fused_red = grad && form == LRNR_FAST && prec == LRNR_FP32 &&
                          tiles <= 2 * (int64_t)m->num_sms;
   if (fused_red) {
     p.fast_regs = 2;
     ps.grid_cap = (int)std::min<int64_t>(tiles, 2 * (int64_t)m->num_sms);
-    scr_bytes = fast_scratch_floats(m->L, p.RM, p.RH, p.nt, ps.grid_cap) * sizeof(float);
+    scr_bytes = (p.fastk ? fastk_scratch_floats(m->L, p.RH, ps.grid_cap)
+                         : fast_scratch_floats(m->L, p.RM, p.RH, p.nt, ps.grid_cap)) *
+                sizeof(float);
   }
   const int64_t n_groups = (tiles + kRedGroup - 1) / kRedGroup;
   const size_t off_part = align256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));

@@ -20,6 +20,7 @@
 #include "lrnr_internal.cuh"
 #include "point_common.cuh"
 #include "simt_common.cuh"
+#include "fused_reduce.cuh"
 
 namespace lrnr {
 namespace {
@@ -28,10 +29,12 @@ constexpr int KT = 128;   // threads (points) per tile
 
 // Shared memory (floats): the reduced pack, s, the maps K (L blocks of RH x RH; K^0 in
 // columns 0..1 of block 0) and k, the per-warp G accumulators (L blocks of RH x RH and
-// g), and one partial row per warp.
+// g), one partial row per warp, the tile offsets and their scan when the kernel
+// computes them (fused_inst instances), and the per-warp sums and flag of the fused
+// reduction.
 struct KfLayout {
-  int pack, s, K, kout, G, red, total;
-  __host__ __device__ KfLayout(int L, int RM, int RH, int P) {
+  int pack, s, K, kout, G, red, toff, scan, misc, total;
+  __host__ __device__ KfLayout(int L, int RM, int RH, int P, int fused_inst) {
     pack = 0;
     s = (fast_pack_floats(L, RM, RH) + 3) & ~3;
     K = (s + (L + 1) * RM + 3) & ~3;
@@ -39,7 +42,10 @@ struct KfLayout {
     G = (kout + RH + 3) & ~3;
     const int gw = L * RH * RH + RH;
     red = G + (KT / 32) * gw;
-    total = red + (KT / 32) * P;
+    toff = red + (KT / 32) * P;
+    scan = toff + (fused_inst ? fused_inst + 1 : 0);
+    misc = scan + (fused_inst ? KT : 0);
+    total = misc + KT / 32 + 1;
   }
   __host__ __device__ static int g_floats(int L, int RH) { return L * RH * RH + RH; }
 };
@@ -261,13 +267,15 @@ __device__ void fastk_tile(const KParams &p, const Tile &T, const float *__restr
   (void)GW;
 }
 
-template <int RM, int RH>
+// FR: the variant with the fixed-order reduction and Adam inside the kernel (group
+// tickets), for batches whose tiles fit in one round of the grid.
+template <int RM, int RH, bool FR>
 __global__ void __launch_bounds__(KT, 2) k_fastk(const __grid_constant__ KParams p) {
   static_assert(RH == 8 || RH == 16, "reduced width");
   extern __shared__ __align__(16) float smem[];
   const int tid = threadIdx.x;
   const int L = p.L;
-  const KfLayout lay(L, RM, RH, p.P);
+  const KfLayout lay(L, RM, RH, p.P, p.fused_tiles ? p.n_inst : 0);
   float *w_s = smem + lay.pack;
   float *s_s = smem + lay.s;
   float *K_s = smem + lay.K;
@@ -281,13 +289,29 @@ __global__ void __launch_bounds__(KT, 2) k_fastk(const __grid_constant__ KParams
   const int LS = fast_layer_floats(RM, RH);
   const int npack = fast_pack_floats(L, RM, RH);
   for (int i = tid; i < npack; i += KT) w_s[i] = __ldg(p.pack + i);
-  if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
+  // Adam step number: the fused reduction reads the counter here and advances it
+  // once every instance is done; otherwise block 0 advances it for the next kernel
+  if (!FR && p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
+  const int64_t kstep = (FR && p.step) ? *p.step + 1 : 0;
+  float *wsum = smem + lay.misc;
+  int *flag = reinterpret_cast<int *>(smem + lay.misc + KT / 32);
   __syncthreads();   // the pack is read by every thread below
   const float *V0 = w_s + L * LS;
   const float Uout = V0[2 * R1];
-  const int ntiles = __ldg(p.tile_off + p.n_inst);
+  const int32_t *toff = p.tile_off;
+  if (p.fused_tiles) {
+    int32_t *toff_s = reinterpret_cast<int32_t *>(smem + lay.toff);
+    block_tile_offsets(p, toff_s, reinterpret_cast<int32_t *>(smem + lay.scan));
+    toff = toff_s;
+  }
+  const int ntiles = p.fused_tiles ? toff[p.n_inst] : __ldg(p.tile_off + p.n_inst);
+  if constexpr (FR) {
+    // instances without points have no tile: finish them here
+    for (int i = blockIdx.x; i < p.n_inst; i += gridDim.x)
+      if (toff[i] == toff[i + 1]) fast_finish_instance(p, i, toff, red_s, wsum, kstep);
+  }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const Tile T = decode_tile(p, tile);
+    const Tile T = decode_tile(p, tile, toff);
     __syncthreads();
     for (int j = tid; j < (L + 1) * RM; j += KT) {
       const int l = j / RM, k = j % RM;
@@ -393,30 +417,37 @@ __global__ void __launch_bounds__(KT, 2) k_fastk(const __grid_constant__ KParams
         p.partial[(int64_t)tile * p.P + j] = acc;
       }
       l2_discard(store, fastk_store_floats(L, RH) * sizeof(float));
+      if constexpr (FR) fast_tile_done(p, tile, ntiles, toff, red_s, wsum, flag, kstep);
     }
   }
 }
 
-template <int RM, int RH>
-cudaError_t launch_fastk_t(const KParams &p, int grid, cudaStream_t st) {
-  const KfLayout lay(p.L, RM, RH, p.P);
+template <int RM, int RH, bool FR>
+cudaError_t launch_fastk_v(const KParams &p, int grid, cudaStream_t st) {
+  const KfLayout lay(p.L, RM, RH, p.P, p.fused_tiles ? p.n_inst : 0);
   const size_t bytes = (size_t)lay.total * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_fastk<RM, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_fastk<RM, RH, FR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_fastk<RM, RH><<<std::max(1, grid), KT, bytes, st>>>(p);
+  k_fastk<RM, RH, FR><<<std::max(1, grid), KT, bytes, st>>>(p);
   return cudaGetLastError();
 }
 
 template <int RM, int RH>
+cudaError_t launch_fastk_t(const KParams &p, int grid, cudaStream_t st) {
+  return p.fused_red ? launch_fastk_v<RM, RH, true>(p, grid, st)
+                     : launch_fastk_v<RM, RH, false>(p, grid, st);
+}
+
+template <int RM, int RH>
 int fastk_ctas_per_sm_t(const KParams &p) {
-  const KfLayout lay(p.L, RM, RH, p.P);
+  const KfLayout lay(p.L, RM, RH, p.P, p.fused_tiles ? p.n_inst : 0);
   const size_t bytes = (size_t)lay.total * sizeof(float);
-  if (cudaFuncSetAttribute(k_fastk<RM, RH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_fastk<RM, RH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes) != cudaSuccess)
     return 1;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fastk<RM, RH>, KT, bytes) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fastk<RM, RH, false>, KT, bytes) !=
       cudaSuccess)
     return 1;
   return std::max(1, per_sm);
@@ -424,9 +455,9 @@ int fastk_ctas_per_sm_t(const KParams &p) {
 
 }  // namespace
 
-bool fastk_supported(int L, int RM, int RH, int P) {
+bool fastk_supported(int L, int RM, int RH, int P, int fused_inst) {
   if ((RM != 32 && RM != 64) || (RH != 8 && RH != 16) || L < 1) return false;
-  const KfLayout lay(L, RM, RH, P);
+  const KfLayout lay(L, RM, RH, P, fused_inst);
   return (size_t)lay.total * sizeof(float) <= (size_t)kSmemBudget;
 }
 

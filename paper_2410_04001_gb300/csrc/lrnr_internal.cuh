@@ -258,8 +258,10 @@ cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_
 // grid_cap bounds the persistent grid (never more CTAs than tiles); the FastLRNR
 // kernel is launched with exactly `grid` CTAs (its scratch is sized for them).
 cudaError_t launch_fast(const KParams &p, int grid, cudaStream_t st);
-// FastLRNR FP32 in reduced coordinates for padded ranks 32 and 64 (RH 8 or 16).
-bool fastk_supported(int L, int RM, int RH, int P);
+// FastLRNR FP32 in reduced coordinates for padded ranks 32 and 64 (RH 8 or 16);
+// fused_inst > 0: the layout with the tile offsets of that many instances in shared
+// memory (KParams::fused_tiles).
+bool fastk_supported(int L, int RM, int RH, int P, int fused_inst);
 int fastk_nt();
 size_t fastk_scratch_floats(int L, int RH, int grid);
 int fastk_ctas_per_sm(const KParams &p);

@@ -100,3 +100,26 @@ def test_high_rank_spinprop_matches_oracle_adam(P):
         assert np.max(np.abs(s[i].cpu().numpy() - sr)) <= 1e-2 * disp + 1e-6, i
         assert abs(lo[i].item() - lr_) <= 1e-4 * abs(lr_) + 1e-6, i
     assert P.lrnr_last_device_status(model) == 0
+
+
+@pytest.mark.parametrize("loss", ["mse", "l1"])
+def test_high_rank_fastlrnr_beyond_one_grid_round(P, loss):
+    """More tiles than two CTAs per SM: the tile kernel writes per-tile partial rows and a
+    separate fixed-order reduction follows (small batches reduce inside the kernel)."""
+    n_int = [12000, 9000, 12000, 11000]
+    net, bt, rows, Xis = case(5, 96, (1, 49, 30, 25, 1), 5, n_int, [64, 0, 40, 10],
+                              [33, 9, 0, 20], (2.0, 1.0, 1.0))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles = sum(-(-a // 128) + -(-b // 128) + -(-c // 64)
+                for a, b, c in zip(n_int, [64, 0, 40, 10], [33, 9, 0, 20]))
+    assert tiles > 2 * sms
+    fnet = lrnr64.make_fast(net, rows, Xis)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    install_fast(P, model, rows, Xis)
+    lo, ds, dbb = P.lrnr_residual_grad(model, "fast", "fp32", P.DeviceBatch.from_host(bt), loss=loss)
+    ro, rs, rb = lrnr64.residual_grad(fnet, bt, "fast", loss=loss)
+    for i in range(bt.n_inst):
+        assert abs(lo[i].item() - ro[i]) <= TOL_FP32 * abs(ro[i]), i
+        assert rel(ds[i].cpu(), rs[i]) < TOL_FP32, (i, rel(ds[i].cpu(), rs[i]))
+        assert rel(dbb[i].cpu(), rb[i]) < TOL_FP32, (i, rel(dbb[i].cpu(), rb[i]))
+    assert P.lrnr_last_device_status(model) == 0
