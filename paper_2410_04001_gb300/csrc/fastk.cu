@@ -151,7 +151,6 @@ __device__ void fastk_tile(const KParams &p, const Tile &T, const float *__restr
   if (!residual_and_seeds(p, T, pt, tid, u, ub, lp)) return;
 
   const int DB0 = partial_db0(L, RM);
-  const int GW = KfLayout::g_floats(L, RH);
   {
     const float ls = warp_sum(lp);
     const float s1 = warp_sum(ub[0]);
@@ -264,7 +263,6 @@ __device__ void fastk_tile(const KParams &p, const Tile &T, const float *__restr
         for (int j = 0; j < RH; ++j) wb[c][j] = nb[c][j];
     }
   }
-  (void)GW;
 }
 
 // FR: the variant with the fixed-order reduction and Adam inside the kernel (group
