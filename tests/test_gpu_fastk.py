@@ -123,3 +123,29 @@ def test_high_rank_fastlrnr_beyond_one_grid_round(P, loss):
         assert rel(ds[i].cpu(), rs[i]) < TOL_FP32, (i, rel(ds[i].cpu(), rs[i]))
         assert rel(dbb[i].cpu(), rb[i]) < TOL_FP32, (i, rel(dbb[i].cpu(), rb[i]))
     assert P.lrnr_last_device_status(model) == 0
+
+
+def test_high_rank_fastlrnr_empty_instance_and_adam(P):
+    """An instance without points gets a zero loss and gradient, and Adam leaves its s
+    where it is (its locality term is zero at the anchor); the others match the oracle."""
+    net, bt, rows, Xis = case(3, 64, (1, 49, 30, 25, 1), 5, [40, 0, 25], [6, 0, 3], [4, 0, 2],
+                              (2.0, 1.0, 1.0))
+    fnet = lrnr64.make_fast(net, rows, Xis)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    install_fast(P, model, rows, Xis)
+    db = P.DeviceBatch.from_host(bt)
+    lo, ds, dbb = P.lrnr_residual_grad(model, "fast", "fp32", db, loss="mse")
+    ro, rs, rb = lrnr64.residual_grad(fnet, bt, "fast", loss="mse")
+    assert lo[1].item() == 0.0 and torch.all(ds[1] == 0) and torch.all(dbb[1] == 0)
+    for i in (0, 2):
+        assert abs(lo[i].item() - ro[i]) <= TOL_FP32 * abs(ro[i]), i
+        assert rel(ds[i].cpu(), rs[i]) < TOL_FP32, i
+    s = torch.tensor(bt.s, dtype=torch.float32, device="cuda")
+    s1 = s[1].clone()
+    m, v = torch.zeros_like(s), torch.zeros_like(s)
+    step = torch.zeros(1, dtype=torch.int64, device="cuda")
+    P.spinprop_step(model, "fast", "fp32", db, s, m, v, step, n_steps=3, lr=1e-2, lambda_loc=1e-3,
+                    s_anchor=s.clone(), loss="l1")
+    assert step.item() == 3
+    assert torch.equal(s[1], s1)
+    assert P.lrnr_last_device_status(model) == 0
