@@ -70,7 +70,7 @@ def dense_loss_grad(net, inst, loss="mse", w=(1.0, 1.0, 1.0)):
     gs = torch.autograd.grad(Ltot, s_t + b_t)
     ds = torch.cat(gs[:net.L + 1]).numpy()
     db = torch.cat(gs[net.L + 1:]).numpy()
-    return float(Ltot), ds, db
+    return float(Ltot.detach()), ds, db
 
 
 def relerr(a, b):

@@ -14,7 +14,8 @@ def declared_functions():
     for fn in sorted(os.listdir(HEADER_DIR)):
         if not fn.endswith(".h"):
             continue
-        src = open(os.path.join(HEADER_DIR, fn)).read()
+        with open(os.path.join(HEADER_DIR, fn)) as fh:
+            src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for m in re.finditer(r"^(?:const\s+)?(?:lrnr_status|void|char|int)\s*\*?\s*(\w+)\s*\(", src, re.M):
             names.append(m.group(1))
