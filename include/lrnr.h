@@ -253,6 +253,9 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec,
  *     race on it and must be serialised by the caller.
  *   Requires every hidden layer selected (fastlrnr_select_rows), else
  *     LRNR_ENOTREADY; the model's own workspace is not used or grown.
+ *   Ranks: padded ranks 8 and 16 (the rank-r FastLRNR kernel); the
+ *     reduced-coordinate kernel for padded ranks 32 and 64 runs only through
+ *     lrnr_residual_grad and spinprop_step, and here returns LRNR_ENOTSUP.
  */
 lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batch *bt, lrnr_loss loss,
                                        const float *w, float *loss_out, float *dL_ds,
