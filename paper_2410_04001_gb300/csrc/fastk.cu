@@ -16,7 +16,10 @@
 // point adds its rhat x rhat products to G (summed over the warp by reduce-scatter,
 // then over the warps in a fixed order), and the rank-r projection runs once per
 // tile.  The partial row per tile has the layout of the rank-r kernel's, so the same
-// reductions follow.
+// reductions follow: a separate fixed-order reduction for large batches, or (FR) the
+// group-ticket reduction and Adam inside this kernel when the batch's tiles fit in
+// one round of the grid, which with the tile offsets computed here makes a small
+// SPInProp step a single launch.
 #include "lrnr_internal.cuh"
 #include "point_common.cuh"
 #include "simt_common.cuh"
