@@ -55,9 +55,10 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per launch of the FastLRNR kernel on this workload, from
-# one ncu capture of the current kernel (profiles/k_fast_cdr_single_m256_r16.md): the
-# mean of three launches of dram__bytes_read.sum + dram__bytes_write.sum.
-K_FAST_DRAM_BYTES = 53_415_424
+# one ncu capture of the current kernel (the mean of three launches of
+# dram__bytes_read.sum + dram__bytes_write.sum), or None while the kernel has
+# changed since the last capture.
+K_FAST_DRAM_BYTES = None
 
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128
@@ -92,20 +93,24 @@ def full_flops_per_point(r, M, channels):
 # --------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock and throttle reasons while the timed region
+    runs.  Every GPU nvidia-smi lists is sampled (no --id: its id forms differ between
+    driver versions); stop() keeps the lines of the GPU whose UUID torch reports, or
+    all lines when nvidia-smi lists a single GPU."""
+    QUERY = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, uuid):
+        self.uuid = (uuid or "").lower().replace("gpu-", "")
         self.proc = None
         self.lines = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -127,10 +132,14 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
+        rows = [[x.strip() for x in ln.split(",")] for ln in self.lines]
+        rows = [f for f in rows if len(f) >= 9]
+        uuids = {f[0].lower().replace("gpu-", "") for f in rows}
+        if self.uuid in uuids:
+            rows = [f for f in rows if f[0].lower().replace("gpu-", "") == self.uuid]
+        elif len(uuids) > 1:
+            rows = []          # several GPUs and none is ours: report no samples
+        for f in rows:
             try:
                 sm.append(float(f[1]))
                 mx = float(f[2])
@@ -710,9 +719,9 @@ def main():
     P.lrnr_timing_read(model)
     step_counter[0] = 0          # the first timed step is one of the eager, event-timed ones
     try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
-        gpu_id = str(local)
+        gpu_id = ""
     clocks = ClockSampler(gpu_id)
     clocks.start()
     if dist:
@@ -750,6 +759,9 @@ def main():
         mp = {"unavailable": str(e)}
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": K_FAST_DRAM_BYTES,
+            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu "
+                             "capture of this kernel on this workload (a constant of that capture)"
+                             if K_FAST_DRAM_BYTES else "no ncu capture of the current kernel yet"),
             "microbench": mp,
             "kernel": "k_fast<16,16> (fused FastLRNR residual + adjoint)",
             "kernel_ms": k_avg_ms, "flops_per_launch": flops_launch,

@@ -69,12 +69,14 @@ typedef enum {
 typedef enum {
   LRNR_FP32 = 0,        /* FP32 SIMT everywhere (reference precision of the GPU path) */
   LRNR_TF32 = 1,        /* tcgen05 kind::tf32: operands rounded to TF32 (10-bit mantissa,
-                           nearest), FP32 accumulation in TMEM (both forms; ranks up
-                           to 32) */
+                           nearest), FP32 accumulation in TMEM (both forms; padded
+                           ranks up to 32) */
   LRNR_BF16 = 2,        /* tcgen05 BF16 operands, FP32 accumulation in TMEM (both forms;
                            the reduced network is an LRNR of width rhat, Sec. 2.2 Eq. 2.8) */
-  LRNR_BF16X3 = 3       /* split-BF16: activations hi + lo, bases hi + mid + lo, products
-                           hi*hi + hi*mid + lo*hi + hi*lo + lo*mid, FP32 accumulation */
+  LRNR_BF16X3 = 3       /* split-BF16 (bf16 x 3): every operand as three BF16 pieces
+                           hi + mid + lo, the six products with piece orders adding up to
+                           at most two (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid),
+                           FP32 accumulation in TMEM; full width: padded ranks 16 and 32 */
 } lrnr_precision;
 
 typedef enum { LRNR_FULL = 0, LRNR_FAST = 1 } lrnr_form;
@@ -86,7 +88,20 @@ typedef struct lrnr_model lrnr_model;
  * A batch of PDE instances and their collocation points (Sec. 3.2 Eq. 3.5-3.6,
  * Sec. 4 Eq. 4.1).  All arrays are device memory; instance i owns the points
  * [off[i], off[i+1]) of each class.  Totals are host values and must equal
- * int_off[n_inst], ic_off[n_inst], bc_off[n_inst].
+ * int_off[n_inst], ic_off[n_inst], bc_off[n_inst].  The kernels check the offsets
+ * on the device: offsets that decrease, start below zero or end past the totals
+ * make the call process no point (outputs zero; spinprop_step applies its Adam
+ * update with a zero loss gradient) and record LRNR_EINVAL for
+ * lrnr_last_device_status.
+ *
+ * norm (optional, device int64 [n_inst][3]): the denominators of the three MSE
+ * means of Eq. 3.5 per instance (interior, initial, periodic), used in place of
+ * the instance's own counts in this batch.  The gradient is a sum over collocation
+ * points (Sec. 2.3), so when one instance's points are split across several calls
+ * (ranks of a data-parallel run), each call given the whole instance's counts
+ * returns partial losses and gradients that add up to the instance's; NULL = the
+ * counts in this batch.  A count must be >= 1 where the batch has points of that
+ * class.  L1 losses (plain sums) ignore it.
  */
 typedef struct {
   int32_t n_inst;                 /* number of instances (mu, s pairs), >= 1 */
@@ -99,6 +114,7 @@ typedef struct {
   const float *x_int, *t_int;     /* device [n_int]: interior points (x, t) */
   const float *x_ic;              /* device [n_ic]: initial points (x, 0), target sin x */
   const float *t_bc;              /* device [n_bc]: periodic pairs (0, t) and (2pi, t) */
+  const int64_t *norm;            /* device [n_inst][3] MSE denominators, or NULL (see above) */
 } lrnr_batch;
 
 /*
@@ -228,31 +244,35 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec,
 /*
  * lrnr_residual_grad_noalloc -- the FastLRNR FP32 loss and gradient of
  * lrnr_residual_grad (form LRNR_FAST, precision LRNR_FP32, same arguments and
- * results), for callers that cannot allocate device memory: code that runs
- * while a stream is being captured into a CUDA graph in global mode (cudaMalloc
- * is refused there), applications whose device memory belongs to another
- * allocator or a fixed budget, and latency-critical loops that cannot afford the
- * device-wide synchronisation of cudaMalloc / cudaFree.  It allocates nothing:
- * its scratch (tile offsets, per-tile partial sums and the kernel's per-CTA
- * layer-input store) is a fixed 32 MiB array in the library's device image, held
- * by every GPU that loads the library until the process exits.  The paper has no
- * counterpart; this is an interface option.
- *   Capacity: 4*(n_inst+1) bytes (rounded up to 256) plus one partial row of
- *     4*(1 + (L+1)*RM + L*RH + 1) bytes per tile of 128 points, plus the store of
- *     at least one CTA (4*4*(L-1)*RM*128 bytes), must fit in 32 MiB (RM, RH: rank
- *     and EIM rows rounded up to 8 or 16); larger batches return LRNR_ETOOBIG
- *     before any GPU work.  The grid shrinks to the CTAs whose stores fit, so
- *     large batches run on fewer SMs; results do not depend on the grid.  At
- *     L = 5, r = rhat = 16 the batch limit is about 5.8 million points.
+ * results), for callers that cannot allocate device memory: applications whose
+ * device memory belongs to another allocator or is held to a fixed budget, and
+ * latency-critical loops that cannot afford the device-wide synchronisation of
+ * cudaMalloc / cudaFree.  It allocates nothing: its scratch (tile offsets,
+ * per-tile partial sums and the kernel's per-CTA layer store) is a fixed 32 MiB
+ * array in the library's device image, held by every GPU that loads the library
+ * until the process exits.  The paper has no counterpart; this is an interface
+ * option.
+ *   Capacity: 4*(n_inst+1) bytes (rounded up to 256), plus one partial row of
+ *     4*(1 + (L+1)*RM + L*RH + 1) bytes per tile of nt points (nt = 128 unless
+ *     lrnr_set_tuning chose 32 or 64; a periodic tile holds nt/2 pairs), plus the
+ *     layer store of at least one CTA, 4*(4*(L-1)*RM + 4*L*RH)*nt bytes, must fit
+ *     in 32 MiB (RM, RH: rank and EIM rows rounded up to 8 or 16); larger batches
+ *     return LRNR_ETOOBIG before any GPU work.  The grid is capped at the CTAs
+ *     whose stores fit in what the partial rows leave of the 32 MiB, so large
+ *     batches run on fewer SMs (at L = 5, r = rhat = 16, nt = 128 a store is
+ *     288 KiB: at most 113 CTAs fit beside no partial rows); results do not depend
+ *     on the grid.  At L = 5, r = rhat = 16 the batch limit is about 5.9 million
+ *     points (one CTA's store left).
  *   Set-up: the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current.
  *   Sharing: every call uses the same array and leaves its contents behind (all
  *     of it is rewritten before it is read, nothing relies on zeros); calls whose
  *     kernels overlap on the GPU (different streams, or several host threads)
  *     race on it and must be serialised by the caller.
  *   Requires every hidden layer selected (fastlrnr_select_rows), else
- *     LRNR_ENOTREADY; the model's own workspace is not used or grown.
+ *     LRNR_ENOTREADY; the model's own workspace is not used or grown.  The tile
+ *     size, CTA cap (lrnr_set_tuning) and wait cap (lrnr_set_wait_limit) of the
+ *     model apply as in lrnr_residual_grad.
  *   Ranks: padded ranks 8 and 16 (the rank-r FastLRNR kernel); the
  *     reduced-coordinate kernel for padded ranks 32 and 64 runs only through
  *     lrnr_residual_grad and spinprop_step, and here returns LRNR_ENOTSUP.
@@ -260,6 +280,26 @@ lrnr_status spinprop_step(lrnr_model *m, lrnr_form form, lrnr_precision prec,
 lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batch *bt, lrnr_loss loss,
                                        const float *w, float *loss_out, float *dL_ds,
                                        float *dL_db, void *stream);
+
+/*
+ * lrnr_adam_update -- one Adam step on s from a given gradient: the update of
+ * spinprop_step (Sec. 4; l1 locality subgradient of Eq. 3.7 when s_anchor != NULL)
+ * applied to dL/ds computed elsewhere, e.g. the sum over ranks of the partial
+ * gradients of one instance whose collocation points are split across GPUs
+ * (lrnr_residual_grad with lrnr_batch.norm, then an all-reduce).
+ *   grad     : device [n_inst][sum_r] dL/ds.
+ *   s_inout, adam_m, adam_v : device [n_inst][sum_r], updated in place.
+ *   step     : device int64 [1]; the update uses k = *step + 1 and then advances it.
+ *   loss_in  : device [n_inst] or NULL; loss_out (device [n_inst] or NULL) receives
+ *              loss_in + lambda_loc * sum |s - s_anchor| at the s before the update.
+ * Two kernel launches on `stream`, no allocation, no host synchronisation.
+ * Errors: LRNR_EINVAL for null arrays, n_inst or sum_r < 1, or hyper-parameters out
+ * of range (as spinprop_step); LRNR_ECUDA if a launch fails.
+ */
+lrnr_status lrnr_adam_update(int32_t n_inst, int32_t sum_r, const float *grad, float *s_inout,
+                             float *adam_m, float *adam_v, int64_t *step, float lr, float beta1,
+                             float beta2, float eps, float lambda_loc, const float *s_anchor,
+                             const float *loss_in, float *loss_out, void *stream);
 
 /* lrnr_reserve -- size the workspace for batches of up to max_points collocation
  * points (interior + initial + 2 x pairs) in up to max_inst instances.  Call it
@@ -319,7 +359,8 @@ typedef struct {
 lrnr_status lrnr_measure_peaks(lrnr_peaks *out, void *stream);
 
 /* lrnr_last_device_status -- synchronises the device, returns and clears the
- * status word written by kernels (LRNR_OK if none). */
+ * status word written by kernels (LRNR_OK if none): LRNR_ENONFINITE, LRNR_ETIMEOUT,
+ * LRNR_ESINGULAR, or LRNR_EINVAL for batch offsets that failed the device check. */
 lrnr_status lrnr_last_device_status(lrnr_model *m);
 
 const char *lrnr_status_string(lrnr_status s);

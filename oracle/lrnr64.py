@@ -238,13 +238,20 @@ def _sign(v):
     return np.sign(v)  # sign(0) = 0
 
 
-def instance_loss_grad(fwd, bwd, model, inst, loss="mse", w=(1.0, 1.0, 1.0)):
+def instance_loss_grad(fwd, bwd, model, inst, loss="mse", w=(1.0, 1.0, 1.0), counts=None):
     """Loss, dL/ds and dL/db of one PDE instance.
 
     ``fwd``/``bwd`` select the full or the reduced network.  The loss is
     ``w_int mean R^2 + w_ic mean B_ic^2 + w_bc mean B_bc^2`` (MSE, Eq. 3.5) or
     ``w_int sum|R| + w_ic sum|B_ic| + w_bc sum|B_bc|`` (l1, Eq. 3.6).  A term whose
     point set is empty is absent.
+
+    ``counts`` = (N_int, N_ic, N_bc), optional: the MSE terms become
+    ``w sum(.^2) / N`` with these denominators instead of the means over the points
+    given.  Evaluated on a subset of an instance's points with the whole
+    instance's counts, this is that subset's share of the instance's loss and
+    gradient: Eq. 3.5's means are sums over the collocation points divided by the
+    point counts, and the gradient is a sum over points (Sec. 2.3).
     """
     s = inst["s"]
     beta, nu, rho = inst["beta"], inst["nu"], inst["rho"]
@@ -261,7 +268,10 @@ def instance_loss_grad(fwd, bwd, model, inst, loss="mse", w=(1.0, 1.0, 1.0)):
     if ni:
         uu = u[:ni]
         R = cdr_residual(uu[:, CH_U], uu[:, CH_T], uu[:, CH_X], uu[:, CH_XX], beta, nu, rho)
-        if loss == "mse":
+        if loss == "mse" and counts is not None:
+            total += w[0] * np.sum(R * R) / counts[0]
+            g = 2.0 * w[0] * R / counts[0]
+        elif loss == "mse":
             total += w[0] * np.mean(R * R)
             g = 2.0 * w[0] * R / ni
         else:
@@ -273,7 +283,10 @@ def instance_loss_grad(fwd, bwd, model, inst, loss="mse", w=(1.0, 1.0, 1.0)):
         ubar[:ni, CH_XX] = -nu * g
     if nc:
         B = u[ni:ni + nc, CH_U] - np.sin(xc)
-        if loss == "mse":
+        if loss == "mse" and counts is not None:
+            total += w[1] * np.sum(B * B) / counts[1]
+            ubar[ni:ni + nc, CH_U] = 2.0 * w[1] * B / counts[1]
+        elif loss == "mse":
             total += w[1] * np.mean(B * B)
             ubar[ni:ni + nc, CH_U] = 2.0 * w[1] * B / nc
         else:
@@ -282,7 +295,10 @@ def instance_loss_grad(fwd, bwd, model, inst, loss="mse", w=(1.0, 1.0, 1.0)):
     if nb:
         o = ni + nc
         B = u[o:o + nb, CH_U] - u[o + nb:o + 2 * nb, CH_U]
-        if loss == "mse":
+        if loss == "mse" and counts is not None:
+            total += w[2] * np.sum(B * B) / counts[2]
+            g = 2.0 * w[2] * B / counts[2]
+        elif loss == "mse":
             total += w[2] * np.mean(B * B)
             g = 2.0 * w[2] * B / nb
         else:
@@ -294,12 +310,15 @@ def instance_loss_grad(fwd, bwd, model, inst, loss="mse", w=(1.0, 1.0, 1.0)):
     return float(total), ds, np.concatenate(db)
 
 
-def residual_grad(model, batch, form="full", loss="mse", w=(1.0, 1.0, 1.0)):
-    """Per-instance loss (n_inst,), dL/ds (n_inst, sum r), dL/db (n_inst, L*M+1)."""
+def residual_grad(model, batch, form="full", loss="mse", w=(1.0, 1.0, 1.0), counts=None):
+    """Per-instance loss (n_inst,), dL/ds (n_inst, sum r), dL/db (n_inst, L*M+1).
+    ``counts`` (n_inst, 3), optional: each instance's MSE denominators (see
+    :func:`instance_loss_grad`)."""
     fwd, bwd = (full_forward, full_backward) if form == "full" else (fast_forward, fast_backward)
     losses, dss, dbs = [], [], []
     for i in range(batch.n_inst):
-        l_, ds, db = instance_loss_grad(fwd, bwd, model, batch.instance(i), loss, w)
+        ci = None if counts is None else counts[i]
+        l_, ds, db = instance_loss_grad(fwd, bwd, model, batch.instance(i), loss, w, ci)
         losses.append(l_)
         dss.append(ds)
         dbs.append(db)

@@ -41,6 +41,7 @@ class lrnr_batch(ctypes.Structure):
         ("int_off", ctypes.c_void_p), ("ic_off", ctypes.c_void_p), ("bc_off", ctypes.c_void_p),
         ("x_int", ctypes.c_void_p), ("t_int", ctypes.c_void_p),
         ("x_ic", ctypes.c_void_p), ("t_bc", ctypes.c_void_p),
+        ("norm", ctypes.c_void_p),
     ]
 
 
@@ -59,6 +60,9 @@ _SIGS = {
                                      _P, _P, _P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
     "lrnr_residual_grad_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "lrnr_adam_update": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P,
+                                        ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
     "lrnr_reserve": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "lrnr_model_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "lrnr_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -214,13 +218,17 @@ def lrnr_last_device_status(model: Model) -> int:
 
 class DeviceBatch:
     """Device copies of a batch (float32 points and parameters, int64 offsets) and
-    the ``lrnr_batch`` struct that points at them."""
+    the ``lrnr_batch`` struct that points at them.  ``norm`` (optional, int64
+    (n_inst, 3)): the MSE denominators of each instance (interior, initial,
+    periodic), for a batch that holds one shard of the instances' points."""
 
-    def __init__(self, n_inst, beta, nu, rho, s, int_off, ic_off, bc_off, x_int, t_int, x_ic, t_bc):
+    def __init__(self, n_inst, beta, nu, rho, s, int_off, ic_off, bc_off, x_int, t_int, x_ic, t_bc,
+                 norm=None):
         self.tensors = dict(beta=beta, nu=nu, rho=rho, s=s, int_off=int_off, ic_off=ic_off,
                             bc_off=bc_off, x_int=x_int, t_int=t_int, x_ic=x_ic, t_bc=t_bc)
         for k, v in self.tensors.items():
             setattr(self, k, v)
+        self.norm = norm
         self.n_inst = n_inst
         self.struct = lrnr_batch()
         self.refresh()
@@ -234,19 +242,26 @@ class DeviceBatch:
         for k in ("beta", "nu", "rho", "s", "int_off", "ic_off", "bc_off", "x_int", "t_int", "x_ic", "t_bc"):
             t = getattr(self, k)
             setattr(st, k, t.data_ptr() if t is not None and t.numel() else None)
+        if self.norm is not None:
+            if self.norm.dtype != torch.int64 or tuple(self.norm.shape) != (self.n_inst, 3) \
+                    or not self.norm.is_contiguous():
+                raise ValueError("norm must be a contiguous int64 tensor of shape (n_inst, 3)")
+            st.norm = self.norm.data_ptr()
+        else:
+            st.norm = None
 
     def with_s(self, s):
         """A batch sharing these points but reading coefficients from ``s``."""
         t = dict(self.tensors)
         t["s"] = s
-        return DeviceBatch(self.n_inst, **t)
+        return DeviceBatch(self.n_inst, **t, norm=self.norm)
 
     @property
     def n_points(self) -> int:
         return int(self.x_int.numel() + self.x_ic.numel() + 2 * self.t_bc.numel())
 
     @classmethod
-    def from_host(cls, bt, device="cuda", s=None, pin=False):
+    def from_host(cls, bt, device="cuda", s=None, pin=False, norm=None):
         f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32))
         i64 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.int64))
         host = dict(beta=f32(bt.beta), nu=f32(bt.nu), rho=f32(bt.rho),
@@ -256,7 +271,9 @@ class DeviceBatch:
         if pin:
             host = {k: v.pin_memory() for k, v in host.items()}
         dev = {k: v.to(device, non_blocking=pin) for k, v in host.items()}
-        return cls(bt.n_inst, **dev)
+        nd = None if norm is None else torch.as_tensor(
+            np.ascontiguousarray(norm, dtype=np.int64)).to(device)
+        return cls(bt.n_inst, **dev, norm=nd)
 
 
 def lrnr_snapshots(model: Model, layer: int, x, t, s, stream=None):
@@ -372,9 +389,9 @@ def lrnr_residual_grad(model: Model, form: str, prec: str, batch: DeviceBatch, l
 def lrnr_residual_grad_noalloc(model: Model, batch: DeviceBatch, loss: str = "mse", w=None,
                                want_db: bool = True, stream=None, out=None):
     """FastLRNR FP32 loss and gradient computed without any device allocation: the
-    library's fixed 8 MiB scratch replaces the model workspace (for callers that
-    cannot allocate, e.g. inside a global-mode graph capture).  Output buffers are
-    still the caller's; pass ``out`` to reuse them."""
+    library's fixed 32 MiB scratch replaces the model workspace (for callers whose
+    device memory belongs to another allocator or a fixed budget).  Output buffers
+    are still the caller's; pass ``out`` to reuse them."""
     dev = batch.x_int.device
     if out is None:
         out = (torch.empty(batch.n_inst, dtype=torch.float32, device=dev),
@@ -400,4 +417,18 @@ def spinprop_step(model: Model, form: str, prec: str, batch: DeviceBatch, s, m, 
                              float(beta1), float(beta2), float(eps), float(lambda_loc),
                              _ptr(s_anchor), _ptr(loss_out), _stream(stream))
     _check(rc, "spinprop_step")
+    return s
+
+
+def lrnr_adam_update(grad, s, m, v, step, lr: float = 1e-3, beta1: float = 0.9,
+                     beta2: float = 0.999, eps: float = 1e-8, lambda_loc: float = 0.0,
+                     s_anchor=None, loss_in=None, loss_out=None, stream=None):
+    """One Adam step on ``s`` (in place) from the gradient ``grad`` (n_inst, sum_r),
+    advancing the device step counter ``step``; ``loss_out`` = ``loss_in`` plus the
+    locality term."""
+    n_inst, sum_r = (int(grad.shape[0]), int(grad.shape[1])) if grad.dim() == 2 else (1, int(grad.numel()))
+    rc = lib().lrnr_adam_update(n_inst, sum_r, _ptr(grad), _ptr(s), _ptr(m), _ptr(v), _ptr(step),
+                                float(lr), float(beta1), float(beta2), float(eps), float(lambda_loc),
+                                _ptr(s_anchor), _ptr(loss_in), _ptr(loss_out), _stream(stream))
+    _check(rc, "lrnr_adam_update")
     return s

@@ -24,7 +24,12 @@ void full_tc_pack(int L, int M, int RM, int NC, const std::vector<std::vector<do
                   const std::vector<std::vector<double>> &V, const std::vector<std::vector<double>> &b,
                   const int *r, std::vector<unsigned char> &out, int tf32);
 int full_tc_nt();
+int full_tc_nc(int RM, int prec);
 size_t full_tc_scratch_floats(int L, int RM, int grid);
+cudaError_t launch_adam_update(int n_inst, int sum_r, const float *g, float *s, float *m, float *v,
+                               int64_t *step, float lr, float b1, float b2, float eps, float lam,
+                               const float *anchor, const float *loss_in, float *loss_out,
+                               cudaStream_t st);
 }  // namespace lrnr
 
 using namespace lrnr;
@@ -43,6 +48,7 @@ struct lrnr_model {
   int *r_dev = nullptr;
   int64_t *offs_dev = nullptr;
   void *tc_pack = nullptr;                     // tensor-core operand pack (full form)
+  void *tc16_pack = nullptr;                   // the same in 16-column chunks (split-BF16, rank 32)
   void *ftc_pack = nullptr;                    // tensor-core pack of the reduced network
   void *tf_pack = nullptr;                     // the same two packs in TF32
   void *ftf_pack = nullptr;
@@ -288,6 +294,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
   p.beta = bt->beta; p.nu = bt->nu; p.rho = bt->rho; p.s = s;
   p.int_off = bt->int_off; p.ic_off = bt->ic_off; p.bc_off = bt->bc_off;
   p.x_int = bt->x_int; p.t_int = bt->t_int; p.x_ic = bt->x_ic; p.t_bc = bt->t_bc;
+  p.tot[0] = bt->n_int; p.tot[1] = bt->n_ic; p.tot[2] = bt->n_bc;
+  p.norm = bt->norm;
   p.grad = grad ? 1 : 0;
   p.status = m->status_dev;
   if (form == LRNR_FAST && tc_prec(prec)) {
@@ -348,9 +356,9 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
         p.nt = tn;
     } else if (tc_prec(prec)) {
       p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
-      if (!(prec == LRNR_TF32 ? m->tf_pack : m->tc_pack) ||
-          !full_tc_supported(m->L, m->M, p.RM, 32, prec))
-        return LRNR_ENOTSUP;
+      const int nc = full_tc_nc(p.RM, prec);
+      const void *pk = prec == LRNR_TF32 ? m->tf_pack : (nc == 16 ? m->tc16_pack : m->tc_pack);
+      if (!pk || !full_tc_supported(m->L, m->M, p.RM, nc, prec)) return LRNR_ENOTSUP;
       p.pack = nullptr;
       p.nt = full_tc_nt();
     } else {
@@ -463,9 +471,10 @@ lrnr_status run_main(lrnr_model *m, lrnr_form form, lrnr_precision prec, Pass &p
   }
   if (tc_prec(prec)) {
     const bool fast = form == LRNR_FAST;
+    const int nc = fast ? m->ftc_nc : full_tc_nc(p.RM, prec);
     const void *pk = prec == LRNR_TF32 ? (fast ? m->ftf_pack : m->tf_pack)
-                                       : (fast ? m->ftc_pack : m->tc_pack);
-    CK(launch_full_tc(p, pk, (int)prec, fast ? m->ftc_nc : 32, ps.grid_cap, st));
+                                       : (fast ? m->ftc_pack : (nc == 16 ? m->tc16_pack : m->tc_pack));
+    CK(launch_full_tc(p, pk, (int)prec, nc, ps.grid_cap, st));
   } else if (form == LRNR_FAST) {
     CK(launch_fast(p, ps.grid_cap, st));
   } else {
@@ -589,6 +598,13 @@ lrnr_status lrnr_build(int L, int M, const int *r, const double *const *U, const
     full_tc_pack(L, M, std::max(16, RM), 32, m->U, m->V, m->b, m->r, tp, 0);
     if ((e = cudaMalloc(&m->tc_pack, tp.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(m->tc_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+  }
+  if (full_tc_supported(L, M, std::max(16, RM), 16, LRNR_BF16X3) &&
+      full_tc_nc(std::max(16, RM), LRNR_BF16X3) == 16) {
+    std::vector<unsigned char> tp;
+    full_tc_pack(L, M, std::max(16, RM), 16, m->U, m->V, m->b, m->r, tp, 0);
+    if ((e = cudaMalloc(&m->tc16_pack, tp.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(m->tc16_pack, tp.data(), tp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
   }
   if (full_tc_supported(L, M, std::max(16, RM), 32, LRNR_TF32)) {
     std::vector<unsigned char> tp;
@@ -834,6 +850,8 @@ lrnr_status noalloc_fast_params(lrnr_model *m, const lrnr_batch *bt, lrnr_loss l
   p.beta = bt->beta; p.nu = bt->nu; p.rho = bt->rho; p.s = bt->s;
   p.int_off = bt->int_off; p.ic_off = bt->ic_off; p.bc_off = bt->bc_off;
   p.x_int = bt->x_int; p.t_int = bt->t_int; p.x_ic = bt->x_ic; p.t_bc = bt->t_bc;
+  p.tot[0] = bt->n_int; p.tot[1] = bt->n_ic; p.tot[2] = bt->n_bc;
+  p.norm = bt->norm;
   p.grad = 1;
   p.status = m->status_dev;
   p.RM = m->fRM;
@@ -841,18 +859,26 @@ lrnr_status noalloc_fast_params(lrnr_model *m, const lrnr_batch *bt, lrnr_loss l
   p.pack = m->fast_pack;
   for (int l = 0; l < m->L; ++l) p.rh[l] = m->rhat[l];
   p.P = partial_len(m->L, p.RM, m->L * p.RH);
-  // same tile size as lrnr_residual_grad, so both give identical results
-  p.nt = fast_choose_nt(m->L, p.RM, p.RH, partial_len(m->L, p.RM, m->L * p.RH + 1));
+  // the tile size and wait cap lrnr_residual_grad uses (including an lrnr_set_tuning
+  // override that fits the kernel's shared memory), so both give identical results
+  const int Pfit = partial_len(m->L, p.RM, m->L * p.RH + 1);
+  p.nt = fast_choose_nt(m->L, p.RM, p.RH, Pfit);
   if (!p.nt) return LRNR_ENOTSUP;
+  const int tn = m->tune_nt[LRNR_FAST][LRNR_FP32];
+  if (tn && fast_smem_bytes(m->L, p.RM, p.RH, tn, Pfit) <= (size_t)kSmemBudget) p.nt = tn;
+  p.fast_regs = m->tune_cta[LRNR_FAST][LRNR_FP32] >= 3 ? 3 : 2;
   p.loss = loss;
   p.w[0] = p.w[1] = p.w[2] = 1.0f;
   if (w) { p.w[0] = w[0]; p.w[1] = w[1]; p.w[2] = w[2]; }
-  p.max_wait = 1u << 20;
+  p.max_wait = m->wait_limit;
   *rows = m->rows_dev;
   *sum_m = m->sum_m;
   *device = m->device;
   return LRNR_OK;
 }
+
+// Cap on resident FastLRNR FP32 CTAs per SM set by lrnr_set_tuning (0 = none).
+int noalloc_cta_cap(const lrnr_model *m) { return m->tune_cta[LRNR_FAST][LRNR_FP32]; }
 
 int64_t noalloc_max_tiles(const lrnr_batch *bt, int nt) {
   return max_tiles(bt->n_int, bt->n_ic, bt->n_bc, bt->n_inst, nt);
@@ -881,6 +907,20 @@ lrnr_status lrnr_reserve(lrnr_model *m, int64_t max_points, int32_t max_inst) {
   lrnr_status rc = ensure_tickets(m, tiles / kRedGroup + 2 + 2 * (int64_t)max_inst, nullptr);
   if (rc != LRNR_OK) return rc;
   return ensure_ws(m, need, nullptr);
+}
+
+lrnr_status lrnr_adam_update(int32_t n_inst, int32_t sum_r, const float *grad, float *s_inout,
+                             float *adam_m, float *adam_v, int64_t *step, float lr, float beta1,
+                             float beta2, float eps, float lambda_loc, const float *s_anchor,
+                             const float *loss_in, float *loss_out, void *stream) {
+  if (n_inst < 1 || sum_r < 1 || !grad || !s_inout || !adam_m || !adam_v || !step) return LRNR_EINVAL;
+  if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f) || !(lambda_loc >= 0.0f))
+    return LRNR_EINVAL;
+  CK(launch_adam_update(n_inst, sum_r, grad, s_inout, adam_m, adam_v, step, lr, beta1, beta2, eps,
+                        s_anchor ? lambda_loc : 0.0f, s_anchor, loss_in, loss_out,
+                        static_cast<cudaStream_t>(stream)));
+  return LRNR_OK;
 }
 
 lrnr_status lrnr_set_wait_limit(lrnr_model *m, int64_t polls) {
@@ -961,6 +1001,7 @@ lrnr_status lrnr_last_device_status(lrnr_model *m) {
     case DEV_NONFINITE: return LRNR_ENONFINITE;
     case DEV_TIMEOUT: return LRNR_ETIMEOUT;
     case DEV_SINGULAR: return LRNR_ESINGULAR;
+    case DEV_BADBATCH: return LRNR_EINVAL;
   }
   return LRNR_ECUDA;
 }
@@ -973,6 +1014,7 @@ void lrnr_destroy(lrnr_model *m) {
   cudaFree(m->r_dev);
   cudaFree(m->offs_dev);
   cudaFree(m->tc_pack);
+  cudaFree(m->tc16_pack);
   cudaFree(m->ftc_pack);
   cudaFree(m->tf_pack);
   cudaFree(m->ftf_pack);

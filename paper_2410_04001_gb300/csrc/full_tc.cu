@@ -39,11 +39,12 @@ int full_tc_supported(int L, int M, int RM, int NC, int prec) {
   if (prec != LRNR_BF16 && prec != LRNR_BF16X3 && prec != LRNR_TF32) return 0;
   // rank 64: BF16, 32-column chunks only
   if (RM == 64 && (prec != LRNR_BF16 || NC == 16)) return 0;
+  // split-BF16 keeps its chunk activations and the running sum of its chunks in
+  // tensor memory (14 NC + 8 RM <= 512 columns): 16-column chunks
+  if (prec == LRNR_BF16X3 && NC == 32) return 0;
   auto pick = [&](auto l16, auto l32) { return RM == 16 ? l16 : l32; };
   int bytes;
   if (RM == 64) bytes = TcLayout<64, 1, 32>::bytes(L);
-  else if (NC == 32 && prec == LRNR_BF16X3)
-    bytes = pick(TcLayout<16, 3, 32>::bytes(L), TcLayout<32, 3, 32>::bytes(L));
   else if (NC == 32 && prec == LRNR_TF32)
     bytes = pick(TcLayout<16, 2, 32>::bytes(L), TcLayout<32, 2, 32>::bytes(L));
   else if (NC == 32) bytes = pick(TcLayout<16, 1, 32>::bytes(L), TcLayout<32, 1, 32>::bytes(L));
@@ -52,9 +53,14 @@ int full_tc_supported(int L, int M, int RM, int NC, int prec) {
   else if (prec == LRNR_TF32)
     bytes = pick(TcLayout<16, 2, 16>::bytes(L), TcLayout<32, 2, 16>::bytes(L));
   else bytes = pick(TcLayout<16, 1, 16>::bytes(L), TcLayout<32, 1, 16>::bytes(L));
-  // (16-column chunks run two CTAs per SM where their shared memory allows, else one)
+  // (16-column chunks run two CTAs per SM where their shared and tensor memory
+  // allow, else one)
   return bytes <= 227 * 1024 ? 1 : 0;
 }
+
+// Chunk width of the full-width network on the tensor cores for a padded rank and
+// precision: 32 columns, 16 for split-BF16 (see full_tc_supported).
+int full_tc_nc(int RM, int prec) { (void)RM; return prec == LRNR_BF16X3 ? 16 : 32; }
 
 int full_tc_nt() { return TNT; }
 
@@ -138,11 +144,10 @@ cudaError_t launch_full_tc(const KParams &p, const void *tc_pack, int prec, int 
   if (prec == LRNR_TF32) return launch_full_tc_tf32(p, tc_pack, NC, grid_cap, st);
   const bool split = prec == LRNR_BF16X3;
   if (NC == 32) {
-    if (p.RM == 16) return split ? launch_tc_t<16, 3, 32>(p, tc_pack, grid_cap, st)
-                                 : launch_tc_t<16, 1, 32>(p, tc_pack, grid_cap, st);
-    if (p.RM == 32) return split ? launch_tc_t<32, 3, 32>(p, tc_pack, grid_cap, st)
-                                 : launch_tc_t<32, 1, 32>(p, tc_pack, grid_cap, st);
-    if (p.RM == 64 && !split) return launch_tc_t<64, 1, 32>(p, tc_pack, grid_cap, st);
+    if (split) return cudaErrorInvalidValue;
+    if (p.RM == 16) return launch_tc_t<16, 1, 32>(p, tc_pack, grid_cap, st);
+    if (p.RM == 32) return launch_tc_t<32, 1, 32>(p, tc_pack, grid_cap, st);
+    if (p.RM == 64) return launch_tc_t<64, 1, 32>(p, tc_pack, grid_cap, st);
   } else if (NC == 16) {
     if (p.RM == 16) return split ? launch_tc_t<16, 3, 16>(p, tc_pack, grid_cap, st)
                                  : launch_tc_t<16, 1, 16>(p, tc_pack, grid_cap, st);

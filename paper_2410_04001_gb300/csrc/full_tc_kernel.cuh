@@ -13,11 +13,19 @@
 //             zb_c = qb'_c Vn_chunk^T                GEMM3  (M=128, N=NC, K=r)
 //             ab_c = adjoint of the tanh jet         epilogue; column sums give dL/db
 //             pb_c += ab_c U_chunk                   GEMM4  (M=128, N=r, K=NC)
-// with one MMA per jet channel c (value, d/dt, d/dx, d2/dx2).  Split-BF16 keeps the
-// activations as hi + lo and the bases as hi + mid + lo (exact to 2^-24) and
-// accumulates five BF16 products per contraction.  TF32 (kind::tf32) takes 32-bit
-// operands rounded to a 10-bit mantissa: twice the shared memory and half the K of a
-// BF16 MMA, so twice the MMAs per contraction.
+// with one MMA per jet channel c (value, d/dt, d/dx, d2/dx2).  Split-BF16 keeps
+// every operand as three BF16 pieces hi + mid + lo (exact to about 2^-27) and
+// accumulates the six products whose pieces' orders add up to at most two (hi hi,
+// hi mid, mid hi, hi lo, lo hi, mid mid; the three dropped ones are below 2^-24
+// relative); its chunk activations, the A operands of GEMM2 and GEMM4, are written
+// by the epilogue to tensor memory (tcgen05.st) and read from there by the MMAs, so
+// that the three pieces of the rank-r operands fit in shared memory.  The tensor
+// core rounds its FP32 accumulation toward zero, so that a long accumulation drifts;
+// split-BF16 therefore accumulates GEMM2 / GEMM4 afresh in every 16-column chunk and
+// adds the chunks' rank-r results into a running FP32 sum (tensor memory) on the
+// CUDA cores, rounding to nearest.  TF32
+// (kind::tf32) takes 32-bit operands rounded to a 10-bit mantissa: twice the shared
+// memory and half the K of a BF16 MMA, so twice the MMAs per contraction.
 //
 // Eight warps: warps w and w+4 share TMEM lanes 32(w%4).. and split each chunk's
 // epilogue columns; warps 0-3 also do the per-point work.  Thread 0 issues the
@@ -49,8 +57,9 @@ constexpr int NTH = 256;   // threads: two per point (column halves of a chunk)
 // SM) or 16 (narrow networks such as the FastLRNR reduced layers: two CTAs and 256
 // TMEM columns each per SM, so that one CTA's epilogue overlaps the other's MMAs; with
 // rank 64 the rank-r accumulators alone take 256 columns and one CTA runs per SM).
-template <int NC, int RM>
-constexpr int tmem_cols() { return (NC == 16 && RM <= 32) ? 256 : 512; }
+// Split-BF16 adds its chunk activations (12 x NC/2 columns) and takes 512 columns.
+template <int NC, int RM, int PREC>
+constexpr int tmem_cols() { return (NC == 16 && RM <= 32 && PREC != 3) ? 256 : 512; }
 
 // Chunk block of the packed bases (bytes), three equal groups of PIECE bytes: the
 // hi pieces of Ub (NC x RM), Vb (NC x RM), Utb (RM x NC), Vtb (RM x NC) followed by
@@ -74,14 +83,21 @@ struct TcLayout {
   static constexpr int HC = NC / 2;                 // columns per epilogue thread
   static constexpr int ES = elem_bytes<PREC>();     // bytes per operand element
   static constexpr int KPM = 32 / ES;               // K elements per MMA (32 bytes of a row)
-  static constexpr int PARTS = PREC == 3 ? 2 : 1;   // activation pieces
+  static constexpr int PARTS = PREC == 3 ? 3 : 1;   // pieces of each operand
   static constexpr int A1B = TNT * RM * ES;         // one (channel, piece) rank-r operand
   static constexpr int A24B = TNT * NC * ES;        // one (channel, piece) width operand
+  static constexpr bool A24_TMEM = PREC == 3;       // chunk activations in tensor memory
   static constexpr int BBYTES = PREC == 3 ? Pk<RM, NC>::ALL : Pk<RM, NC, ES>::HI;
   static constexpr int OFF_A1 = 0;
   static constexpr int OFF_A3 = OFF_A1 + 4 * PARTS * A1B;
   static constexpr int OFF_A24 = OFF_A3 + 4 * PARTS * A1B;
-  static constexpr int OFF_B = OFF_A24 + 4 * PARTS * A24B;
+  static constexpr int OFF_B = OFF_A24 + (A24_TMEM ? 0 : 4 * A24B);
+  // tensor-memory columns: D1 [4][NC], D3 [4][NC], D24 [4][RM], then (split-BF16) the
+  // chunk activations [4 channels][3 pieces][NC/2] (two BF16 per column) and the
+  // running sum R24 [4][RM] of the chunks' rank-r results
+  static constexpr int TM_A24 = 8 * NC + 4 * RM;
+  static constexpr int TM_R24 = TM_A24 + 6 * NC;
+  static constexpr int TM_END = A24_TMEM ? TM_R24 + 4 * RM : TM_A24;
   static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
   static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
   static constexpr int OFF_F = OFF_B + NB * BSTRIDE;
@@ -119,22 +135,28 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
 }
 
 // Store 8 consecutive K entries (k0 a multiple of 8) of one row of a K-major operand
-// with K columns: BF16 (and, for split-BF16, the rounded remainder into the lo piece)
-// or TF32 (round to nearest).
+// with K columns: BF16, the three BF16 pieces of split-BF16 (piece i at base + i *
+// pstride), or TF32 (round to nearest).
 template <int PREC>
-__device__ __forceinline__ void put8(unsigned char *hi_base, unsigned char *lo_base, int row,
-                                     int k0, int K, const float (&w)[8]) {
+__device__ __forceinline__ void put8(unsigned char *base, uint32_t pstride, int row, int k0, int K,
+                                     const float (&w)[8]) {
   if constexpr (PREC == 2) {
-    *reinterpret_cast<uint4 *>(hi_base + tc::kmajor_off_e(row, k0, K, 4)) =
+    *reinterpret_cast<uint4 *>(base + tc::kmajor_off_e(row, k0, K, 4)) =
         tc::pack4_tf32(w[0], w[1], w[2], w[3]);
-    *reinterpret_cast<uint4 *>(hi_base + tc::kmajor_off_e(row, k0 + 4, K, 4)) =
+    *reinterpret_cast<uint4 *>(base + tc::kmajor_off_e(row, k0 + 4, K, 4)) =
         tc::pack4_tf32(w[4], w[5], w[6], w[7]);
+  } else if constexpr (PREC == 3) {
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tc::split3_bf16x2(w[2 * i], w[2 * i + 1], h[i], m[i], l[i]);
+    const uint32_t off = tc::kmajor_off(row, k0, K);
+    *reinterpret_cast<uint4 *>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(base + pstride + off) = make_uint4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<uint4 *>(base + 2 * pstride + off) = make_uint4(l[0], l[1], l[2], l[3]);
   } else {
     uint4 hi, lo;
     tc::pack8_bf16(w, hi, lo);
-    const uint32_t off = tc::kmajor_off(row, k0, K);
-    *reinterpret_cast<uint4 *>(hi_base + off) = hi;
-    if constexpr (PREC == 3) *reinterpret_cast<uint4 *>(lo_base + off) = lo;
+    *reinterpret_cast<uint4 *>(base + tc::kmajor_off(row, k0, K)) = hi;
   }
 }
 
@@ -147,32 +169,68 @@ __device__ __forceinline__ void put_rank_row(unsigned char *base, int c, const f
     float w[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) w[i] = v[k0 + i];
-    put8<PREC>(base + (Lay::PARTS * c) * Lay::A1B, base + (2 * c + 1) * Lay::A1B, row, k0, RM, w);
+    put8<PREC>(base + (Lay::PARTS * c) * Lay::A1B, Lay::A1B, row, k0, RM, w);
   }
 }
 
-// D (+)= A B^T with A = Ah (+ Al) and B = Bh (+ Bm + Bl) in BF16 pieces.  BF16:
-// Ah Bh.  Split: Ah Bh + Ah Bm + Al Bh + Ah Bl + Al Bm; the dropped terms are below
-// 2^-25 relative, and the error left is that of the two-piece activation.  TF32: one
-// product of TF32 operands.
+// Pieces (i of A, j of B) of the split-BF16 products, largest first: every pair
+// with i + j <= 2.
+constexpr int kSplitProducts = 6;
+__device__ __forceinline__ constexpr int split_ai(int t) { return t == 2 ? 1 : (t == 4 ? 2 : (t == 5 ? 1 : 0)); }
+__device__ __forceinline__ constexpr int split_bj(int t) { return t == 1 ? 1 : (t == 3 ? 2 : (t == 5 ? 1 : 0)); }
+
+// D (+)= A B^T with A in shared memory (piece i of A at aBase + i * aStride bytes,
+// piece j of B at b + j * PIECE bytes).  BF16: one product.  Split-BF16: the six
+// products hi hi, hi mid, mid hi, hi lo, lo hi, mid mid.  TF32: one product of TF32
+// operands.
 template <int RM, int PREC, int NC>
-__device__ __forceinline__ void mma_split(uint32_t d, uint32_t aHi, uint32_t aLo, uint32_t b,
+__device__ __forceinline__ void mma_split(uint32_t d, uint32_t aBase, uint32_t aStride, uint32_t b,
                                           uint32_t sboA, uint32_t sboB, uint32_t idesc,
                                           uint32_t acc) {
-  const uint64_t ah = tc::sdesc(aHi, 128, sboA);
   if constexpr (PREC == 2) {
-    tc::mma_tf32(d, ah, tc::sdesc(b, 128, sboB), idesc, acc);
-    return;
-  }
-  tc::mma_bf16(d, ah, tc::sdesc(b, 128, sboB), idesc, acc);
-  if constexpr (PREC == 3) {
+    tc::mma_tf32(d, tc::sdesc(aBase, 128, sboA), tc::sdesc(b, 128, sboB), idesc, acc);
+  } else if constexpr (PREC == 3) {
     constexpr uint32_t PC = Pk<RM, NC>::PIECE;
-    const uint64_t al = tc::sdesc(aLo, 128, sboA);
-    const uint64_t bm = tc::sdesc(b + PC, 128, sboB);
-    tc::mma_bf16(d, ah, bm, idesc, 1u);
-    tc::mma_bf16(d, al, tc::sdesc(b, 128, sboB), idesc, 1u);
-    tc::mma_bf16(d, ah, tc::sdesc(b + 2 * PC, 128, sboB), idesc, 1u);
-    tc::mma_bf16(d, al, bm, idesc, 1u);
+#pragma unroll
+    for (int t = 0; t < kSplitProducts; ++t)
+      tc::mma_bf16(d, tc::sdesc(aBase + split_ai(t) * aStride, 128, sboA),
+                   tc::sdesc(b + split_bj(t) * PC, 128, sboB), idesc, t == 0 ? acc : 1u);
+  } else {
+    tc::mma_bf16(d, tc::sdesc(aBase, 128, sboA), tc::sdesc(b, 128, sboB), idesc, acc);
+  }
+}
+
+// Split-BF16 with A in tensor memory (piece i at column aT + i * aCols): the six
+// products of mma_split.
+template <int RM, int NC>
+__device__ __forceinline__ void mma_split_t(uint32_t d, uint32_t aT, uint32_t aCols, uint32_t b,
+                                            uint32_t sboB, uint32_t idesc, uint32_t acc) {
+  constexpr uint32_t PC = Pk<RM, NC>::PIECE;
+#pragma unroll
+  for (int t = 0; t < kSplitProducts; ++t)
+    tc::mma_bf16_ts(d, aT + split_ai(t) * aCols, tc::sdesc(b + split_bj(t) * PC, 128, sboB), idesc,
+                    t == 0 ? acc : 1u);
+}
+
+// Write n consecutive chunk-activation values of channel c (this thread's row, K
+// positions k0..k0+n-1 of the chunk, k0 even) to the tensor-memory A operand of
+// split-BF16: three pieces, two BF16 per column.  n = 16 or 8.
+template <int NC, int n>
+__device__ __forceinline__ void put_act_tmem(uint32_t ta_row, int c, int k0, const float *v) {
+  constexpr int HALF = NC / 2;           // columns per (channel, piece)
+  uint32_t h[n / 2], m[n / 2], l[n / 2];
+#pragma unroll
+  for (int i = 0; i < n / 2; ++i) tc::split3_bf16x2(v[2 * i], v[2 * i + 1], h[i], m[i], l[i]);
+  const uint32_t col = ta_row + (uint32_t)(3 * c * HALF + k0 / 2);
+  if constexpr (n == 16) {
+    tc::tmem_st8(col, h);
+    tc::tmem_st8(col + HALF, m);
+    tc::tmem_st8(col + 2 * HALF, l);
+  } else {
+    static_assert(n == 8, "activation group");
+    tc::tmem_st4(col, h);
+    tc::tmem_st4(col + HALF, m);
+    tc::tmem_st4(col + 2 * HALF, l);
   }
 }
 
@@ -225,6 +283,8 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   const uint32_t sA1u = tc::smem_u32(sA1), sA3u = tc::smem_u32(sA3), sA24u = tc::smem_u32(sA24);
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t D1 = tb, D3 = tb + 4 * NC, D24 = tb + 8 * NC;
+  const uint32_t TA = tb + Lay::TM_A24;   // split-BF16 chunk activations (A of GEMM2 / GEMM4)
+  const uint32_t R24 = tb + Lay::TM_R24;  // split-BF16 running sum of the chunks' GEMM2 / GEMM4
   constexpr uint32_t ID_W = PREC == 2 ? tc::idesc_tf32(128, NC) : tc::idesc_bf16(128, NC);
   constexpr uint32_t ID_R = PREC == 2 ? tc::idesc_tf32(128, RM) : tc::idesc_bf16(128, RM);
   // byte stride between 8-row core-matrix groups: K elements of ES bytes, 8 rows
@@ -248,10 +308,39 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     for (int k0 = 0; k0 < RM; k0 += 16) {
       float w[16];
       tc::tmem_ld16(D24 + lane_base + c * RM + k0, w);
+      if (Lay::A24_TMEM && NCH > 1) {
+        float r[16];
+        tc::tmem_ld16(R24 + lane_base + c * RM + k0, r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w[i] += r[i];
+      }
       tc::tmem_ld_wait();
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[k0 + i] = w[i];
     }
+  };
+  // split-BF16: add the rank-r result of the chunk just finished (D24, accumulated
+  // afresh by each chunk) into R24, rounding to nearest; the first chunk of a layer
+  // initialises R24.  Thread (row, half) takes half of each channel's RM columns.
+  auto fold_chunk = [&](bool first) {
+    constexpr int HR = RM / 2;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+      for (int i0 = 0; i0 < HR; i0 += 8) {
+        const uint32_t col = lane_base + c * RM + half * HR + i0;
+        float d[8], r[8];
+        tc::tmem_ld8(D24 + col, d);
+        if (!first) tc::tmem_ld8(R24 + col, r);
+        tc::tmem_ld_wait();
+        uint32_t w8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w8[i] = __float_as_uint(first ? d[i] : d[i] + r[i]);
+        tc::tmem_st8(R24 + col, w8);
+      }
+    }
+    tc::tmem_st_wait();
   };
   auto stored_c = [&](int l, int c, float (&v)[RM]) {   // input jet of layer l >= 1
 #pragma unroll
@@ -293,6 +382,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     for (int j = 0; j < NCH; ++j) {
       const int n = n0 + j;
       if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }   // GEMM2(j-1) done
+      if constexpr (Lay::A24_TMEM) if (j > 0) fold_chunk(j == 1);
       if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
       if (!wait_b(n)) { dead = true; return; }
       if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
@@ -306,8 +396,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 #pragma unroll
           for (int kk = 0; kk < RM / KPM; ++kk)
             mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
-                                sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
-                                SBO_R, ID_W, kk > 0);
+                                    Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
         tc::mma_commit(ctl.b1);
       }
       ctl.p1 = true;
@@ -333,16 +422,21 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           }
           a[0][i] = z;
         }
+        if constexpr (Lay::A24_TMEM) {
 #pragma unroll
-        for (int c = 0; c < C; ++c)
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC>(TA + lane_base, c, c0, a[c]);
+          tc::tmem_st_wait();
+        } else {
 #pragma unroll
-          for (int h = 0; h < HC / 8; ++h) {
-            float w8[8];
+          for (int c = 0; c < C; ++c)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
-            put8<PREC>(sA24 + (Lay::PARTS * c) * Lay::A24B, sA24 + (2 * c + 1) * Lay::A24B, row,
-                       c0 + h * 8, NC, w8);
-          }
+            for (int h = 0; h < HC / 8; ++h) {
+              float w8[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
+              put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0 + h * 8, NC, w8);
+            }
+        }
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
@@ -352,10 +446,15 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 #pragma unroll
         for (int c = 0; c < C; ++c)
 #pragma unroll
-          for (int kk = 0; kk < NC / KPM; ++kk)
-            mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
-                                sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 3 * PK::T + kk * 256,
-                                SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+          for (int kk = 0; kk < NC / KPM; ++kk) {
+            if constexpr (Lay::A24_TMEM)
+              mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
+                                  sB + 3 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
+            else
+              mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
+                                      sB + 3 * PK::T + kk * 256, SBO_W, SBO_W, ID_R,
+                                      (j > 0 || kk > 0));
+          }
         tc::mma_commit(ctl.b2);
       }
       ctl.p2 = true;
@@ -435,6 +534,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     for (int j = 0; j < NCH; ++j) {
       const int n = n0 + j;
       if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
+      if constexpr (Lay::A24_TMEM) if (j > 0) fold_chunk(j == 1);
       if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
       if (!wait_b(n)) { dead = true; return; }
       if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
@@ -448,11 +548,9 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 #pragma unroll
           for (int kk = 0; kk < RM / KPM; ++kk) {
             mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
-                                sA1u + (2 * c + 1) * Lay::A1B + kk * 256, sB + kk * 256, SBO_R,
-                                SBO_R, ID_W, kk > 0);
+                                    Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
             mma_split<RM, PREC, NC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
-                                sA3u + (2 * c + 1) * Lay::A1B + kk * 256, sB + PK::T + kk * 256,
-                                SBO_R, SBO_R, ID_W, kk > 0);
+                                    Lay::A1B, sB + PK::T + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
           }
         tc::mma_commit(ctl.b1);
       }
@@ -484,16 +582,20 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           }
           wb[0][i] = ab0;
         }
+        if constexpr (Lay::A24_TMEM) {
 #pragma unroll
-        for (int c = 0; c < C; ++c)
-          put8<PREC>(sA24 + (Lay::PARTS * c) * Lay::A24B, sA24 + (2 * c + 1) * Lay::A24B, row, c0,
-                     NC, wb[c]);
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, 8>(TA + lane_base, c, c0, wb[c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < C; ++c) put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0, NC, wb[c]);
+        }
         float g8[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) g8[i] = wb[0][i];
         const float r = warp_reduce_scatter<8>(g8);
         if ((lane & 3) == 0) dbw[warp * HC + h8 * 8 + (lane >> 2)] = r;
       }
+      if constexpr (Lay::A24_TMEM) tc::tmem_st_wait();
       tc::fence_async_smem();
       tc::fence_before_sync();
       __syncthreads();
@@ -502,10 +604,15 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 #pragma unroll
         for (int c = 0; c < C; ++c)
 #pragma unroll
-          for (int kk = 0; kk < NC / KPM; ++kk)
-            mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + (Lay::PARTS * c) * Lay::A24B + kk * 256,
-                                sA24u + (2 * c + 1) * Lay::A24B + kk * 256, sB + 2 * PK::T + kk * 256,
-                                SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+          for (int kk = 0; kk < NC / KPM; ++kk) {
+            if constexpr (Lay::A24_TMEM)
+              mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
+                                  sB + 2 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
+            else
+              mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
+                                      sB + 2 * PK::T + kk * 256, SBO_W, SBO_W, ID_R,
+                                      (j > 0 || kk > 0));
+          }
         tc::mma_commit(ctl.b2);
       }
       ctl.p2 = true;
@@ -542,9 +649,10 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 }
 
 template <int RM, int PREC, int NC>
-__global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_full_tc(const __grid_constant__ KParams p,
+__global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM, PREC>() == 256) ? 2 : 1) k_full_tc(const __grid_constant__ KParams p,
                                                   const unsigned char *__restrict__ pack) {
   using Lay = TcLayout<RM, PREC, NC>;
+  static_assert(Lay::TM_END <= tmem_cols<NC, RM, PREC>(), "tensor-memory columns");
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x;
   const int L = p.L;
@@ -554,7 +662,7 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_f
   float *red_s = fa + (L + 1) * RM;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((Lay::OFF_F + Lay::floats(L) * 4 + 15) & ~15));
   uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
-  if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC, RM>());
+  if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC, RM, PREC>());
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
     tc::fence_mbar_init();
@@ -604,7 +712,7 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM>() == 256) ? 2 : 1) k_f
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid < 32) tc::tmem_dealloc(tb, tmem_cols<NC, RM>());
+  if (tid < 32) tc::tmem_dealloc(tb, tmem_cols<NC, RM, PREC>());
 }
 
 template <int RM, int PREC, int NC>
@@ -617,8 +725,8 @@ cudaError_t launch_tc_t(const KParams &p, const void *pack, int grid_cap, cudaSt
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // every CTA holds tmem_cols<NC, RM>() TMEM columns: at most 512 / that many per SM
-  const int grid = std::max(1, std::min(grid_cap, sms * (512 / tmem_cols<NC, RM>())));
+  // every CTA holds tmem_cols<NC, RM, PREC>() TMEM columns: at most 512 / that many per SM
+  const int grid = std::max(1, std::min(grid_cap, sms * (512 / tmem_cols<NC, RM, PREC>())));
   k_full_tc<RM, PREC, NC><<<grid, NTH, bytes, st>>>(p, static_cast<const unsigned char *>(pack));
   return cudaGetLastError();
 }

@@ -24,7 +24,9 @@ constexpr float TWO_PI_F = 6.28318530717958647692f;
 enum PointKind { KIND_INT = 0, KIND_IC = 1, KIND_BC = 2 };
 
 // Error codes the kernels write into the device status word (first writer wins).
-enum DevStatus { DEV_OK = 0, DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_SINGULAR = 3 };
+// DEV_BADBATCH: a batch's CSR offsets decrease, start below zero or end past the
+// host totals; no point of the call is processed.
+enum DevStatus { DEV_OK = 0, DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_SINGULAR = 3, DEV_BADBATCH = 4 };
 
 struct KParams {
   int L, M, n_inst;
@@ -38,6 +40,8 @@ struct KParams {
   const float *beta, *nu, *rho, *s;
   const int64_t *int_off, *ic_off, *bc_off;
   const float *x_int, *t_int, *x_ic, *t_bc;
+  int64_t tot[3];              // host totals of interior points, initial points, pairs
+  const int64_t *norm;         // [n_inst][3] MSE denominators, or null: the own counts
   // schedule
   const int32_t *tile_off;     // [n_inst+1]
   int nt;                      // points per tile (pairs per periodic tile: nt/2)
@@ -122,16 +126,36 @@ __device__ __forceinline__ int32_t tiles_of(const int64_t *io, const int64_t *co
   return (int32_t)((nI + nt - 1) / nt + (nC + nt - 1) / nt + (nB + half - 1) / half);
 }
 
+// True when the CSR offsets of instances [b, e) are non-decreasing, and, for the
+// first and last instance, start at or above zero and end at or below the host
+// totals: then every tile reads points inside the caller's arrays and the tile
+// count is within the host bound the workspace was sized for.
+__device__ __forceinline__ bool offsets_ok(const int64_t *io, const int64_t *co, const int64_t *bo,
+                                           const int64_t (&tot)[3], int n_inst, int b, int e) {
+  bool ok = true;
+  for (int i = b; i < e; ++i)
+    ok = ok && io[i + 1] >= io[i] && co[i + 1] >= co[i] && bo[i + 1] >= bo[i];
+  if (b == 0 && e > 0) ok = ok && io[0] >= 0 && co[0] >= 0 && bo[0] >= 0;
+  if (e == n_inst && b < e)
+    ok = ok && io[n_inst] <= tot[0] && co[n_inst] <= tot[1] && bo[n_inst] <= tot[2];
+  return ok;
+}
+
 // Tile offsets computed by one CTA into shared memory (toff_s[n_inst + 1]); used by
 // kernels that fuse the tile schedule.  Block 0 also publishes them to p.tile_off
-// for the reduction kernel that runs next.  Call with all threads of the block.
+// for the reduction kernel that runs next.  A batch whose offsets fail offsets_ok
+// gets no tiles (every offset zero) and DEV_BADBATCH.  Call with all threads of the
+// block.
 __device__ __forceinline__ void block_tile_offsets(const KParams &p, int32_t *toff_s,
                                                    int32_t *scan_s) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int chunk = (p.n_inst + nth - 1) / nth;
-  const int b = tid * chunk, e = min(p.n_inst, b + chunk);
+  const int b = min(p.n_inst, tid * chunk), e = min(p.n_inst, b + chunk);
+  const bool bad =
+      __syncthreads_or(!offsets_ok(p.int_off, p.ic_off, p.bc_off, p.tot, p.n_inst, b, e));
   int32_t acc = 0;
-  for (int i = b; i < e; ++i) acc += tiles_of(p.int_off, p.ic_off, p.bc_off, i, p.nt);
+  if (!bad)
+    for (int i = b; i < e; ++i) acc += tiles_of(p.int_off, p.ic_off, p.bc_off, i, p.nt);
   scan_s[tid] = acc;
   __syncthreads();
   for (int off = 1; off < nth; off *= 2) {
@@ -143,9 +167,10 @@ __device__ __forceinline__ void block_tile_offsets(const KParams &p, int32_t *to
   int32_t run = scan_s[tid] - acc;
   for (int i = b; i < e; ++i) {
     toff_s[i] = run;
-    run += tiles_of(p.int_off, p.ic_off, p.bc_off, i, p.nt);
+    if (!bad) run += tiles_of(p.int_off, p.ic_off, p.bc_off, i, p.nt);
   }
   if (tid == nth - 1) toff_s[p.n_inst] = scan_s[nth - 1];
+  if (bad && blockIdx.x == 0 && tid == 0) set_status(p.status, DEV_BADBATCH);
   __syncthreads();
   if (blockIdx.x == 0)
     for (int i = tid; i <= p.n_inst; i += nth) const_cast<int32_t *>(p.tile_off)[i] = toff_s[i];
@@ -226,19 +251,32 @@ __device__ __forceinline__ void l2_discard(const void *base, size_t bytes) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(b + o) : "memory");
 }
 
-// tanh jet: value z = tanh(a), first derivative d1 = 1 - z^2 and second d2 = -2 z d1,
-// from the identity tanh|a| = 1 - q with q = 2 / (exp(2|a|) + 1) in (0, 1], so that
-// 1 - z^2 = q (2 - q) keeps its relative accuracy where tanh saturates.  exp on the
-// MUFU unit (ex2.approx, relative error about 2^-22) and its reciprocal: z has an
-// absolute error of a few 1e-7 (relative for |a| >= 0.5), d1 a relative error of a
-// few 1e-7.  Large |a| overflows exp to +inf, whose reciprocal is +0 (z = +-1, d1 =
-// 0); a NaN input stays NaN.
+// tanh jet: value z = tanh(a), first derivative d1 = 1 - z^2 and second d2 = -2 z d1.
+// For |a| >= 1/2, from the identity tanh|a| = 1 - q with q = 2 / (exp(2|a|) + 1) in
+// (0, 1], so that 1 - z^2 = q (2 - q) keeps its relative accuracy where tanh
+// saturates; exp on the MUFU unit (ex2.approx, relative error about 2^-22) and its
+// reciprocal give z and d1 to a few 1e-7 relative there.  For |a| < 1/2, where
+// 1 - q cancels, z comes from the Maclaurin series of tanh, whose coefficient of
+// a^(2n-1) is 2^(2n) (2^(2n) - 1) B_2n / (2n)! (B_2n the Bernoulli numbers), taken
+// to a^15: the first omitted term is below 1e-8 of z at |a| = 1/2, and z keeps a
+// relative error of about 1e-7 down to the smallest normal |a| (z = a there; ftz
+// flushes subnormal a to zero).  d1 is q (2 - q) for every a.  Large |a| overflows
+// exp to +inf, whose reciprocal is +0 (z = +-1, d1 = 0); a NaN input stays NaN.
 __device__ __forceinline__ void tanh_d(float a, float &z, float &d1, float &d2) {
   float e, r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fabsf(a) * 2.88539008177792681f));   // 2 / ln 2
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
   const float q = 2.0f * r;
-  z = copysignf(1.0f - q, a);
+  const float a2 = a * a;
+  float c = -929569.0f / 638512875.0f;
+  c = fmaf(a2, c, 21844.0f / 6081075.0f);
+  c = fmaf(a2, c, -1382.0f / 155925.0f);
+  c = fmaf(a2, c, 62.0f / 2835.0f);
+  c = fmaf(a2, c, -17.0f / 315.0f);
+  c = fmaf(a2, c, 2.0f / 15.0f);
+  c = fmaf(a2, c, -1.0f / 3.0f);
+  const float zs = fmaf(a * a2, c, a);
+  z = fabsf(a) < 0.5f ? zs : copysignf(1.0f - q, a);
   d1 = q * (2.0f - q);
   d2 = -2.0f * z * d1;
 }

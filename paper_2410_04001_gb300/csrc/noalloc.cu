@@ -1,12 +1,12 @@
 // Allocation-free FastLRNR FP32 loss and gradient (lrnr_residual_grad_noalloc).
 //
-// Some callers cannot call cudaMalloc: code running inside a global-mode CUDA graph
-// capture, programs whose device memory is owned by another allocator or a fixed
-// budget, and loops that cannot take the device-wide synchronisation of
-// cudaMalloc / cudaFree.  This entry point runs the same three kernels as
-// lrnr_residual_grad(LRNR_FAST, LRNR_FP32) but takes its scratch (tile offsets and
-// per-tile partial sums) from a fixed array in the library's device image instead
-// of the model's workspace.
+// Some callers cannot call cudaMalloc: programs whose device memory is owned by
+// another allocator or held to a fixed budget, and loops that cannot take the
+// device-wide synchronisation of cudaMalloc / cudaFree.  This entry point runs the
+// same kernels as lrnr_residual_grad(LRNR_FAST, LRNR_FP32) (tile offsets, the
+// FastLRNR tile kernel, the fixed-order reduction) but takes its scratch (tile
+// offsets, per-tile partial sums and the per-CTA layer store) from a fixed array in
+// the library's device image instead of the model's workspace.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +19,7 @@ lrnr_status noalloc_fast_params(lrnr_model *m, const lrnr_batch *bt, lrnr_loss l
                                 const float *w, KParams &p, const int32_t **rows, int *sum_m,
                                 int *device);
 int64_t noalloc_max_tiles(const lrnr_batch *bt, int nt);
+int noalloc_cta_cap(const lrnr_model *m);
 }  // namespace lrnr
 
 namespace {
@@ -67,7 +68,7 @@ extern "C" lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batc
   // as many CTAs as the rest of the array holds (at least one)
   const int64_t tiles = noalloc_max_tiles(bt, p.nt);
   const size_t off_part = round256(sizeof(int32_t) * (size_t)(bt->n_inst + 1));
-  if (tiles < 0 || off_part > kScratchBytes ||
+  if (tiles < 0 || tiles > INT32_MAX / 2 || off_part > kScratchBytes ||
       (size_t)tiles * (size_t)p.P * sizeof(float) > kScratchBytes - off_part)
     return LRNR_ETOOBIG;
   const size_t off_store = off_part + round256((size_t)tiles * (size_t)p.P * sizeof(float));
@@ -86,8 +87,10 @@ extern "C" lrnr_status lrnr_residual_grad_noalloc(lrnr_model *m, const lrnr_batc
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t fit = (int64_t)((kScratchBytes - off_store) / per_cta);
+    int per_sm = fast_ctas_per_sm(p);
+    if (noalloc_cta_cap(m) > 0) per_sm = std::min(per_sm, noalloc_cta_cap(m));
     const int grid_cap = (int)std::min<int64_t>(
-        std::min<int64_t>(tiles, (int64_t)fast_ctas_per_sm(p) * sms), fit);
+        std::min<int64_t>(tiles, (int64_t)per_sm * sms), fit);
     cudaError_t e = launch_tile_offsets(p, static_cast<int32_t *>(base), st);
     if (e == cudaSuccess) e = launch_fast(p, grid_cap, st);
     if (e == cudaSuccess && dL_db)

@@ -37,6 +37,16 @@ __device__ __forceinline__ PointIn load_point(const KParams &p, const Tile &T, i
   return pt;
 }
 
+// Denominator of the MSE mean of point class k (0 interior, 1 initial, 2 periodic)
+// of instance inst (Eq. 3.5): the caller's count when the batch carries one (a shard
+// of an instance's points is normalised by the count of the whole instance, so that
+// the shards' losses and gradients add up to the instance's), else the class's own
+// count in this batch.
+__device__ __forceinline__ float mse_count(const KParams &p, int inst, int k, const int64_t *off) {
+  return (float)(p.norm ? __ldg(p.norm + 3 * (int64_t)inst + k)
+                        : __ldg(off + inst + 1) - __ldg(off + inst));
+}
+
 // Given the output jet u = (u, u_t, u_x, u_xx) of the point in `slot`: in
 // evaluation mode write the requested outputs and return false; in gradient mode
 // return true with the point's loss share in lp and the seeds d loss / d u_c in
@@ -63,7 +73,7 @@ __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile 
       }
       return false;
     }
-    const float n = (float)(__ldg(p.int_off + inst + 1) - __ldg(p.int_off + inst));
+    const float n = mse_count(p, inst, 0, p.int_off);
     float gR;
     if (mse) { lp = p.w[0] * R * R / n; gR = 2.0f * p.w[0] * R / n; }
     else { lp = p.w[0] * fabsf(R); gR = p.w[0] * (float)((R > 0.0f) - (R < 0.0f)); }
@@ -78,7 +88,7 @@ __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile 
       if (pt.act && p.res_ic) p.res_ic[T.first + slot] = B;
       return false;
     }
-    const float n = (float)(__ldg(p.ic_off + inst + 1) - __ldg(p.ic_off + inst));
+    const float n = mse_count(p, inst, 1, p.ic_off);
     float gB;
     if (mse) { lp = p.w[1] * B * B / n; gB = 2.0f * p.w[1] * B / n; }
     else { lp = p.w[1] * fabsf(B); gB = p.w[1] * (float)((B > 0.0f) - (B < 0.0f)); }
@@ -91,7 +101,7 @@ __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile 
       if (pt.act && pt.side == 0 && p.res_bc) p.res_bc[T.first + (slot >> 1)] = B;
       return false;
     }
-    const float n = (float)(__ldg(p.bc_off + inst + 1) - __ldg(p.bc_off + inst));
+    const float n = mse_count(p, inst, 2, p.bc_off);
     float gB;
     if (mse) { lp = p.w[2] * B * B / n; gB = 2.0f * p.w[2] * B / n; }
     else { lp = p.w[2] * fabsf(B); gB = p.w[2] * (float)((B > 0.0f) - (B < 0.0f)); }

@@ -7,19 +7,20 @@
 namespace lrnr {
 namespace {
 
-// tile_off[i] = first tile of instance i (exclusive prefix sum); one block.
-__global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *io, const int64_t *co,
-                                                       const int64_t *bo, int n_inst, int nt,
-                                                       int32_t *tile_off, int *status) {
+// tile_off[i] = first tile of instance i (exclusive prefix sum); one block.  A batch
+// whose offsets fail offsets_ok gets no tiles (every offset zero) and DEV_BADBATCH.
+__global__ void __launch_bounds__(1024) k_tile_offsets(const __grid_constant__ KParams p,
+                                                       int32_t *tile_off) {
   __shared__ int32_t sums[1024];
   const int tid = threadIdx.x;
+  const int n_inst = p.n_inst;
+  const int64_t *io = p.int_off, *co = p.ic_off, *bo = p.bc_off;
   const int chunk = (n_inst + 1023) / 1024;
-  const int b = tid * chunk, e = min(n_inst, b + chunk);
+  const int b = min(n_inst, tid * chunk), e = min(n_inst, b + chunk);
+  const bool bad = __syncthreads_or(!offsets_ok(io, co, bo, p.tot, n_inst, b, e));
   int32_t acc = 0;
-  for (int i = b; i < e; ++i) {
-    if (io[i + 1] < io[i] || co[i + 1] < co[i] || bo[i + 1] < bo[i]) set_status(status, DEV_NONFINITE);
-    acc += tiles_of(io, co, bo, i, nt);
-  }
+  if (!bad)
+    for (int i = b; i < e; ++i) acc += tiles_of(io, co, bo, i, p.nt);
   sums[tid] = acc;
   __syncthreads();
   for (int off = 1; off < 1024; off *= 2) {
@@ -31,9 +32,10 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const int64_t *io, const 
   int32_t run = sums[tid] - acc;
   for (int i = b; i < e; ++i) {
     tile_off[i] = run;
-    run += tiles_of(io, co, bo, i, nt);
+    if (!bad) run += tiles_of(io, co, bo, i, p.nt);
   }
   if (tid == 1023) tile_off[n_inst] = sums[1023];
+  if (bad && tid == 0) set_status(p.status, DEV_BADBATCH);
 }
 
 // Sum of column j over the rows t0 + g, t0 + g + 32, ... < t1 of the partial
@@ -347,6 +349,50 @@ __global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
   cl.sync();
 }
 
+// Adam on s from a given gradient (the update of spinprop_step, Sec. 4, with the
+// l1 locality subgradient of Eq. 3.7); block i updates instance i.  The step number
+// is the counter's value plus one (k_step_advance moves the counter afterwards).
+// loss_out[i] = loss_in[i] + lam sum |s - anchor| (the locality term at the s the
+// gradient was taken at), summed in a fixed order.
+__global__ void __launch_bounds__(256) k_adam_update(int sum_r, const float *__restrict__ g,
+                                                     float *s, float *m, float *v,
+                                                     const int64_t *step, float lr, float b1,
+                                                     float b2, float eps, float lam,
+                                                     const float *anchor, const float *loss_in,
+                                                     float *loss_out) {
+  __shared__ float lsh[8];
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const float kstep = (float)(*step + 1);
+  const float bc1 = 1.0f - powf(b1, kstep);
+  const float bc2 = 1.0f - powf(b2, kstep);
+  float loc = 0.0f;
+  for (int q = tid; q < sum_r; q += 256) {
+    const int64_t o = (int64_t)i * sum_r + q;
+    const float sv = s[o];
+    float gr = g[o];
+    if (anchor) {
+      const float d = sv - anchor[o];
+      loc += lam * fabsf(d);
+      gr += lam * (float)((d > 0.0f) - (d < 0.0f));
+    }
+    const float mv = b1 * m[o] + (1.0f - b1) * gr;
+    const float vv = b2 * v[o] + (1.0f - b2) * gr * gr;
+    m[o] = mv;
+    v[o] = vv;
+    s[o] = sv - lr * (mv / bc1) / (sqrtf(vv / bc2) + eps);
+  }
+  loc = warp_sum(loc);
+  if ((tid & 31) == 0) lsh[tid >> 5] = loc;
+  __syncthreads();
+  if (tid == 0 && loss_out) {
+    float lt = 0.0f;
+    for (int w = 0; w < 8; ++w) lt += lsh[w];
+    loss_out[i] = (loss_in ? loss_in[i] : 0.0f) + lt;
+  }
+}
+
+__global__ void k_step_advance(int64_t *step) { *step += 1; }
+
 void fill_red(RedArgs &a, const KParams &p, int n_needed, int fast, const int32_t *rows,
               float *loss_out, float *dL_ds, float *dL_db, int sum_m) {
   a.partial = p.partial;
@@ -371,8 +417,7 @@ void fill_red(RedArgs &a, const KParams &p, int n_needed, int fast, const int32_
 }  // namespace
 
 cudaError_t launch_tile_offsets(const KParams &p, int32_t *tile_off, cudaStream_t st) {
-  k_tile_offsets<<<1, 1024, 0, st>>>(p.int_off, p.ic_off, p.bc_off, p.n_inst, p.nt, tile_off,
-                                     p.status);
+  k_tile_offsets<<<1, 1024, 0, st>>>(p, tile_off);
   return cudaGetLastError();
 }
 
@@ -426,6 +471,18 @@ cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, c
 
 size_t adam_group_floats(int n_inst, int L, int RM) {
   return (size_t)n_inst * kAdamGroups * partial_db0(L, RM);
+}
+
+cudaError_t launch_adam_update(int n_inst, int sum_r, const float *g, float *s, float *m, float *v,
+                               int64_t *step, float lr, float b1, float b2, float eps, float lam,
+                               const float *anchor, const float *loss_in, float *loss_out,
+                               cudaStream_t st) {
+  k_adam_update<<<n_inst, 256, 0, st>>>(sum_r, g, s, m, v, step, lr, b1, b2, eps, lam, anchor,
+                                        loss_in, loss_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_step_advance<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
 }
 
 }  // namespace lrnr

@@ -78,6 +78,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
       : "memory");
 }
 
+// D[tmem] (+)= A * B^T with A (M x 16 BF16, row i in TMEM lane i, K pairs packed
+// two per 32-bit column: 8 columns) in tensor memory and B in shared memory.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // D[tmem] (+)= A * B^T with TF32 operands, one instruction (M x N x 8).
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
@@ -162,6 +174,23 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Store 32 lanes x 32 bits x 8 (or 4) consecutive columns starting at taddr (this
+// warp's lanes); tmem_st_wait() before the stored data is read by an MMA.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+               "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // tanh on the MUFU unit (about 2^-11 relative error): used only where operands are
 // BF16 anyway.
 __device__ __forceinline__ float tanh_approx(float x) {
@@ -184,6 +213,20 @@ __device__ __forceinline__ void pack8_bf16(const float (&v)[8], uint4 &hi, uint4
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Three-piece BF16 split of two floats, packed as BF16 pairs: x = hi + mid + lo +
+// O(2^-27 |x|) with hi = rn(x), mid = rn(x - hi), lo = rn(x - hi - mid) (round to
+// nearest even; each difference is exact in FP32).
+__device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t &hi, uint32_t &mid,
+                                              uint32_t &lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float ra = a - __low2float(h), rb = b - __high2float(h);
+  const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(ra - __low2float(m), rb - __high2float(m));
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  mid = *reinterpret_cast<const uint32_t *>(&m);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // Four floats rounded to TF32 (nearest, ties away from zero), as 16 bytes.

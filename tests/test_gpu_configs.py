@@ -63,10 +63,9 @@ def test_batched_512_instances_fast(P):
         assert rel(dbb[i], rb) < TOL_FP32, i
 
 
-# Jet tolerance per precision at this depth: the split-BF16 activations (hi + lo,
-# about 2^-18 each) leave the derivative channels near 2e-5 of their rounding scale
-# after six layers, so the jets get 3e-5; its gradients keep 1e-5.
-JET_TOL = {"fp32": 1e-5, "bf16x3": 3e-5, "tf32": 2.5e-3, "bf16": 2e-2}
+# Jet tolerance per precision (normwise error over the sampled points, measured
+# against each channel's rounding scale, see gpu_common.jet_magnitudes).
+JET_TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "tf32": 2.5e-3, "bf16": 2e-2}
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-5), ("tf32", 2.5e-3),

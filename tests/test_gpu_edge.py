@@ -57,8 +57,8 @@ def test_network_of_x_minus_beta_t_has_zero_convection_residual(P, form, prec):
     R = out["res"].cpu().numpy()
     assert np.linalg.norm(ux) > 0
     # R = u_t + beta u_x cancels two channels computed independently: its size is the
-    # channels' relative error (FP32 ~1e-7; split-BF16 activations ~2^-17)
-    tol = 1e-5 if prec == "fp32" else 1e-4
+    # channels' relative error (FP32 and split-BF16 ~1e-7)
+    tol = 1e-5
     assert np.linalg.norm(R) <= tol * beta * np.linalg.norm(ux)
 
 

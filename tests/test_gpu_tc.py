@@ -81,18 +81,12 @@ def test_tc_ragged_instances(P):
 @pytest.mark.parametrize("shape", [(3, 96, 16, 16), (4, 64, 8, 11), (2, 80, 32, 16)])
 def test_fast_tc_gradient_matches_oracle(P, prec, shape):
     """The reduced network (width r-hat, Eq. 2.8) on the tensor cores, 16-column
-    chunks and two CTAs per SM: loss, dL/ds and dL/db (scattered to the EIM rows)
-    against the oracle's FastLRNR; r-hat = 11 leaves zero padding rows.
-
-    Rank 32 into 16 rows (the last shape) loses a few more bits to cancellation in
-    the derivative channels: its split-BF16 errors are 1e-5 to 3e-5 (measured), so
-    that shape is held to 3e-5 in split-BF16.  (Narrower still, rank 32 into 8 rows
-    on these random bases, the outputs cancel so much that BF16 is off by 8 % in u
-    and split-BF16 by 7e-5: a property of the operands' precision, not of the
-    kernel, whose split-BF16 error there is still 1,000 times below BF16's.)"""
+    chunks: loss, dL/ds and dL/db (scattered to the EIM rows) against the oracle's
+    FastLRNR; r-hat = 11 leaves zero padding rows; rank 32 into 16 rows runs
+    split-BF16 with its three-piece activations in tensor memory."""
     from tests.gpu_common import eim_for, install_fast
     L, M, r, rh = shape
-    tol = 3e-5 if (prec == "bf16x3" and r == 32) else TOL[prec]
+    tol = TOL[prec]
     net, bt = cdr_case(L=L, M=M, r=r, seed=7 * L + M + rh)
     rows, Xis, _ = eim_for(net, bt.s[0], rh)
     fnet = lrnr64.make_fast(net, rows, Xis)
