@@ -32,6 +32,16 @@ WORKLOAD = ("CDR beta=5 nu=1 rho=2; LRNR L=5 hidden layers, M=256, r=16, tanh; F
             "rhat=16 rows/layer (EIM); 65,536 interior + 2,048 initial + 1,024 periodic pairs")
 
 
+def workload_name(world):
+    """One instance of the CDR problem with world x (65,536 + 2,048 + 1,024 pairs)
+    points; on N ranks each rank takes its block of every point class."""
+    if world == 1:
+        return WORKLOAD
+    return (WORKLOAD.replace("65,536 interior + 2,048 initial + 1,024 periodic pairs",
+                             f"{world} x (65,536 interior + 2,048 initial + 1,024 periodic pairs)")
+            + f", points split over {world} ranks")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,7 +239,7 @@ def run_reference(args):
     import numpy as np
     import synth
     from oracle import adam64, eim64, lrnr64
-    net, bt = synth.workload_cdr_single()
+    net, bt = synth.workload_cdr_single(scale=world)
     g = synth.rng(77)
     xs, ts = synth.snapshot_design(g, 8)
     rows, Xis = [], []
@@ -278,7 +288,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD + f"; FastLRNR SPInProp step on a 1/{stride} point sample",
+        "config": {"workload": workload_name(world) + f"; FastLRNR SPInProp step on a 1/{stride} point sample",
                    "form": "fast"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
                          "sample": f"every {stride}th point of each class ({n_pts} points per step)"},
@@ -646,10 +656,18 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    net, bt = synth.workload_cdr_single()
+    # N ranks: one instance with N x 69,632 points, each rank its block of every point
+    # class, normalised by the whole instance's counts; one all-reduce of (loss, dL/ds)
+    # per step, then the replicated Adam update (weak scaling: per-rank work fixed)
+    from paper_2410_04001_gb300 import shard
+    net, bt = synth.workload_cdr_single(scale=world)
     model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
     dev = torch.device("cuda", local)
-    db = P.DeviceBatch.from_host(bt, dev)
+    if world > 1:
+        part, counts = shard.point_shard(bt, world, rank)
+        db = P.DeviceBatch.from_host(part, dev, norm=counts)
+    else:
+        db = P.DeviceBatch.from_host(bt, dev)
     # FastLRNR construction: exact-LRNR snapshots at the 4 x 3 design plus
     # perturbations (device, FP64), EIM greedy on the device
     g = synth.rng(77)
@@ -671,9 +689,18 @@ def main():
     step_ctr = torch.zeros(1, dtype=torch.int64, device=dev)
     loss_out = torch.zeros(1, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    db_s = db.with_s(s)
+    bufs = shard.partial_buffers(1, model.sum_r, model.sum_m, False, device=dev)
+
+    def step_on(batch, s_, lo_):
+        if world > 1:
+            shard.sharded_spinprop_step(model, "fast", "fp32", batch, s_, m, v, step_ctr, dist,
+                                        bufs=bufs, lr=1e-3, loss_out=lo_)
+        else:
+            P.spinprop_step(model, "fast", "fp32", batch, s_, m, v, step_ctr, 1, lr=1e-3, loss_out=lo_)
 
     def spin():
-        P.spinprop_step(model, "fast", "fp32", db, s, m, v, step_ctr, 1, lr=1e-3, loss_out=loss_out)
+        step_on(db_s, s, loss_out)
 
     # CUDA graph of one step (2 kernels).  Kernel timing: every 8th timed step runs the
     # same step eagerly with the library's timing events around the FastLRNR kernel;
@@ -682,14 +709,17 @@ def main():
     for _ in range(3):
         spin()
     torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
-        spin()
+    graph = None
+    if world == 1:
+        # (at N ranks the step holds an NCCL all-reduce and runs eagerly)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+            spin()
     step_counter = [0]
 
     def replay():
         step_counter[0] += 1
-        if step_counter[0] % 8 == 1:
+        if graph is None or step_counter[0] % 8 == 1:
             spin()
         else:
             graph.replay()
@@ -741,13 +771,15 @@ def main():
         tt = torch.tensor([ms_step], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms_step = float(tt.item())
-    value = world * n_pts / (ms_step * 1e-3)
+    n_total = bt.n_points                      # all ranks' points (= n_pts at N = 1)
+    value = n_total / (ms_step * 1e-3)
 
     # ---- roofline of the dominant kernel (the fused FastLRNR kernel)
     ch = 4
     pf_int = fast_flops_per_point(net.r, [16] * net.L, ch)
     pf_bnd = fast_flops_per_point(net.r, [16] * net.L, 1)
-    flops_launch = bt.x_int.shape[0] * pf_int + (bt.x_ic.shape[0] + 2 * bt.t_bc.shape[0]) * pf_bnd
+    # this rank's launch: its own points (the whole batch at N = 1)
+    flops_launch = (db.x_int.numel() * pf_int + (db.x_ic.numel() + 2 * db.t_bc.numel()) * pf_bnd)
     k_avg_ms = kern_ms / max(1, kern_n)
     peaks, src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -770,8 +802,8 @@ def main():
     # ---- variants: full-width FP32 LRNR residual + gradient, fast residual + gradient
     variants = {}
     P.lrnr_timing(model, True)
-    for form, prec in (("full", "fp32"), ("full", "bf16"), ("full", "tf32"), ("full", "bf16x3"),
-                       ("fast", "fp32"), ("fast", "bf16"), ("fast", "tf32"), ("fast", "bf16x3")):
+    for form, prec in (() if world > 1 else (("full", "fp32"), ("full", "bf16"), ("full", "tf32"), ("full", "bf16x3"),
+                       ("fast", "fp32"), ("fast", "bf16"), ("fast", "tf32"), ("fast", "bf16x3"))):
         try:
             out = P.lrnr_residual_grad(model, form, prec, db)
         except P.LrnrError as e:
@@ -799,7 +831,7 @@ def main():
     P.lrnr_timing(model, False)
 
     # ---- errors against the FP64 oracle (full batch, same inputs)
-    if rank == 0 and not args.no_oracle:
+    if rank == 0 and world == 1 and not args.no_oracle:
         from oracle import lrnr64, eim64
 
         def rel(a, b):
@@ -826,7 +858,7 @@ def main():
             np.array_equal(a, b) for a, b in zip(rows_o, rows_all))
 
     # ---- the larger workloads (one GPU): batched instances and the SPInProp loop
-    if not args.no_configs:
+    if not args.no_configs and world == 1:
         variants.update(config_variants(P, synth, np, torch, dev, timed_steps, peak,
                                         with_oracle=(rank == 0 and not args.no_oracle)))
 
@@ -853,7 +885,8 @@ def main():
     for k in segs:
         view(hbuf, k).copy_(segs[k][1].detach().cpu())
     dv = {k: view(dbuf, k) for k in segs}
-    db_e2e = P.DeviceBatch(db.n_inst, **{k: (dv["s"] if k == "s" else dv[k]) for k in db.tensors})
+    db_e2e = P.DeviceBatch(db.n_inst, **{k: (dv["s"] if k == "s" else dv[k]) for k in db.tensors},
+                           norm=db.norm)
     n_in = segs["s"][0] + s.numel() * 4                     # batch arrays and s
     out_lo, out_hi = segs["s"][0], segs["loss"][0] + loss_out.numel() * 4
     hout = torch.zeros(out_hi - out_lo, dtype=torch.uint8).pin_memory()
@@ -861,8 +894,7 @@ def main():
 
     def e2e_step():
         dbuf[:n_in].copy_(hbuf[:n_in], non_blocking=True)
-        P.spinprop_step(model, "fast", "fp32", db_e2e, dv["s"], m, v, step_ctr, 1, lr=1e-3,
-                        loss_out=dv["loss"])
+        step_on(db_e2e, dv["s"], dv["loss"])
         hout.copy_(dbuf[out_lo:out_hi], non_blocking=True)
 
     for _ in range(3):
@@ -881,18 +913,24 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "FastLRNR SPInProp step (spinprop_step, 1 Adam step)",
-                       "points_per_step": n_pts, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "config": {"workload": workload_name(world),
+                       "form": ("FastLRNR SPInProp step (spinprop_step, 1 Adam step)" if world == 1 else
+                                "FastLRNR SPInProp step on each rank's points (lrnr_residual_grad with "
+                                "the instance's counts, all-reduce of loss and dL/ds, lrnr_adam_update)"),
+                       "points_per_step": n_total,
+                       "parallelism": f"points of one instance split over {world} ranks" if world > 1 else "single GPU",
                        "l2": "flushed before every timed step (256 MiB write)", "cuda_graph": True},
             "roofline": roof,
             "cpu_baseline": cpu_base,
-            "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": "points/s",
+            "e2e": {"value": n_total / (e2e_ms * 1e-3), "unit": "points/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "note": "one pinned host -> device copy of the batch arrays and s, spinprop_step, "
                             "one copy of s and the loss back to host"},
-            # per SPInProp step: the FastLRNR kernel (it computes its own tile schedule
-            # for up to 4,096 instances) and the fixed-order reduction + Adam kernel
-            "gpu_launches": 2 * args.steps,
+            # per SPInProp step at N = 1: the FastLRNR kernel (it computes its own tile
+            # schedule for up to 4,096 instances) and the fixed-order reduction + Adam
+            # kernel; at N ranks: the FastLRNR kernel, the reduction, the Adam update
+            # and the step-counter kernel (the all-reduce is NCCL's)
+            "gpu_launches": (2 if world == 1 else 4) * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
             "device_status": status,
