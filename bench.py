@@ -50,7 +50,68 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
     ap.add_argument("--no-configs", action="store_true", help="skip the batched / SPInProp workloads")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one kernel case --steps times (for profilers) and exit")
     return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- profiling cases
+
+PROFILE_CASES = {
+    "fast_fp32_cdr": "FastLRNR SPInProp step, FP32 (k_fast + reduction / Adam), CDR M=256 r=16 L=5, 69,632 points",
+    "fastk_fp32_paper_d2": "FastLRNR SPInProp step, FP32 reduced coordinates (k_fastk), M=4000 r=(1,49,30,25,1) "
+                           "rhat=5, 65,536 + 2,048 + 1,024 pairs",
+    "full_bf16_cdr": "full-width residual + gradient, BF16 tensor cores (k_full_tc), CDR M=256 r=16 L=5",
+    "full_bf16x3_cdr": "full-width residual + gradient, split-BF16 tensor cores (k_full_tc), CDR M=256 r=16 L=5",
+    "full_fp32_cdr": "full-width residual + gradient, FP32 SIMT (k_full_fp32), CDR M=256 r=16 L=5",
+}
+
+
+def run_profile_case(args):
+    """Build the case's model and batch, run it --warmup + --steps times on the
+    current stream, print one line with the mean CUDA-event time per call."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2410_04001_gb300 as P
+    import synth
+    from paper_2410_04001_gb300 import fastphase
+    dev = torch.device("cuda", 0)
+    case = args.profile_case
+    if case == "fastk_fp32_paper_d2":
+        net, bx, bt = synth.workload_paper_d2()
+    else:
+        net, bt = synth.workload_cdr_single()
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    db = P.DeviceBatch.from_host(bt, dev)
+    g = synth.rng(77)
+    xs, ts = synth.snapshot_design(g, 8)
+    if case.startswith("fast"):
+        s0 = bt.s[:1]
+        fastphase.build_reduced(model, torch.tensor(xs, device=dev), torch.tensor(ts, device=dev),
+                                torch.tensor(s0, device=dev), rhat=5 if case.startswith("fastk") else 16)
+        s = db.s.clone()
+        m, v = torch.zeros_like(s), torch.zeros_like(s)
+        k = torch.zeros(1, dtype=torch.int64, device=dev)
+        fn = lambda: P.spinprop_step(model, "fast", "fp32", db, s, m, v, k, 1, lr=1e-3)
+    else:
+        prec = case.split("_")[1]
+        out = P.lrnr_residual_grad(model, "full", prec, db)
+        fn = lambda: P.lrnr_residual_grad(model, "full", prec, db, out=out)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "what": PROFILE_CASES[case], "points": db.n_points,
+                      "calls": args.steps, "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps),
+                      "device_status": P.lrnr_last_device_status(model)}))
 
 
 # --------------------------------------------------------------------------- peaks
@@ -68,7 +129,7 @@ def measured_peaks():
 # one ncu capture of the current kernel (the mean of three launches of
 # dram__bytes_read.sum + dram__bytes_write.sum), or None while the kernel has
 # changed since the last capture.
-K_FAST_DRAM_BYTES = None
+K_FAST_DRAM_BYTES = 50_330_027
 
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128
@@ -633,6 +694,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_case:
+        run_profile_case(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))
