@@ -61,3 +61,30 @@ def test_captured_spinprop_graph_equals_eager_steps(P):
     torch.cuda.synchronize()
     assert k1.item() == 12 and k2.item() == 12
     assert torch.equal(s1, s2) and torch.equal(m1, m2) and torch.equal(v1, v2)
+
+
+@pytest.mark.parametrize("form", ["fast", "full"])
+def test_autograd_gradient_matches_central_differences_of_the_kernel_loss(P, form):
+    """The gradient behind lrnr_loss against central differences of lrnr_loss itself
+    (FP32 forward), along a random direction of s per instance: (L(s + h d) -
+    L(s - h d)) / 2h = <dL/ds, d> + O(h^2) + O(eps_FP32 L / h); with h = 2e-3 both error
+    terms are below 1e-4 of the derivative, held to 2e-3."""
+    from paper_2410_04001_gb300.autograd import lrnr_loss
+    g = synth.rng(8)
+    net = synth.make_net(g, L=3, M=48, r=8)
+    bt = as_f32_batch(synth.make_instances(g, net, 3, 300, 700))
+    rows, Xis, _ = eim_for(net, bt.s[0], 16)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    install_fast(P, model, rows, Xis)
+    db = P.DeviceBatch.from_host(bt)
+    s = db.s.clone().requires_grad_(True)
+    lrnr_loss(s, model, db, form=form).sum().backward()
+    d = torch.tensor(g.standard_normal(tuple(s.shape)), dtype=torch.float32, device="cuda")
+    d = d / d.norm(dim=1, keepdim=True)
+    h = 2e-3
+    with torch.no_grad():
+        lp = lrnr_loss((s + h * d).contiguous(), model, db, form=form).double()
+        lm = lrnr_loss((s - h * d).contiguous(), model, db, form=form).double()
+    fd = (lp - lm) / (2.0 * h)
+    an = (s.grad.double() * d.double()).sum(dim=1)
+    assert torch.all((fd - an).abs() <= 2e-3 * an.abs().clamp_min(1e-3)), (fd, an)
