@@ -345,15 +345,20 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     p.RM = m->RM;
     p.RH = 0;
     if (prec == LRNR_FP32) {
-      if (p.RM > 32) return LRNR_ENOTSUP;   // the FP32 full-width kernel holds rank <= 32 jets
       p.pack = m->full_pack;
-      p.nt = full_fp32_choose_nt(m->L, p.RM, partial_len(m->L, p.RM, m->L * m->M + 1));
-      if (!p.nt) return LRNR_ENOTSUP;
-      const int tn = m->tune_nt[LRNR_FULL][prec];
-      if ((tn == 32 || tn == 64) &&
-          full_fp32_smem_bytes(m->L, p.RM, tn, partial_len(m->L, p.RM, m->L * m->M + 1)) <=
-              (size_t)kSmemBudget)
-        p.nt = tn;
+      if (p.RM >= 32) {
+        // padded ranks 32 / 64: RM / 16 threads share a point (full_fp32_sliced.cu)
+        if (full_fp32_sl_smem_bytes(m->L, m->M, p.RM) > (size_t)kSmemBudget) return LRNR_ENOTSUP;
+        p.nt = full_fp32_sl_nt(p.RM);
+      } else {
+        p.nt = full_fp32_choose_nt(m->L, p.RM, partial_len(m->L, p.RM, m->L * m->M + 1));
+        if (!p.nt) return LRNR_ENOTSUP;
+        const int tn = m->tune_nt[LRNR_FULL][prec];
+        if ((tn == 32 || tn == 64) &&
+            full_fp32_smem_bytes(m->L, p.RM, tn, partial_len(m->L, p.RM, m->L * m->M + 1)) <=
+                (size_t)kSmemBudget)
+          p.nt = tn;
+      }
     } else if (tc_prec(prec)) {
       p.RM = std::max(16, m->RM);   // tensor-core tiles need K and N of at least 16
       const int nc = full_tc_nc(p.RM, prec);
@@ -395,7 +400,10 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     int per_sm = full_fp32_ctas_per_sm(p);
     if (m->tune_cta[LRNR_FULL][prec] > 0) per_sm = std::min(per_sm, m->tune_cta[LRNR_FULL][prec]);
     ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
-    if (grad) scr_bytes = full_fp32_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap) * sizeof(float);
+    if (grad)
+      scr_bytes = (p.RM >= 32 ? full_fp32_sl_scratch_floats(m->L, p.RM, ps.grid_cap)
+                              : full_fp32_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap)) *
+                  sizeof(float);
   }
   // Batches whose tiles fit in one round of the FastLRNR grid (2 CTAs per SM) are
   // reduced inside the kernel (group rows + tickets): one launch instead of two.

@@ -305,6 +305,13 @@ size_t fastk_scratch_floats(int L, int RH, int grid);
 int fastk_ctas_per_sm(const KParams &p);
 cudaError_t launch_fastk(const KParams &p, int grid, cudaStream_t st);
 cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st);
+// Full-width FP32 at padded ranks 32 and 64: RM / 16 threads per point
+// (full_fp32_sliced.cu); points per tile, shared memory, scratch, occupancy, launch.
+int full_fp32_sl_nt(int RM);
+size_t full_fp32_sl_smem_bytes(int L, int M, int RM);
+size_t full_fp32_sl_scratch_floats(int L, int RM, int grid);
+int full_fp32_sl_ctas_per_sm(const KParams &p);
+cudaError_t launch_full_fp32_sl(const KParams &p, int grid, cudaStream_t st);
 // NC: 32-column chunks (full-width networks, one CTA per SM) or 16-column chunks
 // (narrow networks, two CTAs per SM while RM <= 32).
 cudaError_t launch_full_tc_tf32(const KParams &p, const void *tc_pack, int NC, int grid_cap,

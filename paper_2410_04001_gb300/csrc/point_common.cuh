@@ -48,13 +48,15 @@ __device__ __forceinline__ float mse_count(const KParams &p, int inst, int k, co
 }
 
 // Given the output jet u = (u, u_t, u_x, u_xx) of the point in `slot`: in
-// evaluation mode write the requested outputs and return false; in gradient mode
-// return true with the point's loss share in lp and the seeds d loss / d u_c in
-// ub.  Periodic tiles pair slots (2j, 2j+1) of one warp, so every lane of the
-// warp must call this.
+// evaluation mode write the requested outputs (when `write`) and return false; in
+// gradient mode return true with the point's loss share in lp and the seeds
+// d loss / d u_c in ub.  Periodic tiles pair slots (2j, 2j+1) of one warp, held by
+// lanes pair_xor apart (1 when a thread holds a point, TPP when TPP consecutive
+// threads share one), so every lane of the warp must call this.
 __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile &T,
                                                    const PointIn &pt, int slot, const float (&u)[4],
-                                                   float (&ub)[4], float &lp) {
+                                                   float (&ub)[4], float &lp, int pair_xor = 1,
+                                                   bool write = true) {
   const int inst = T.inst;
   const float beta = __ldg(p.beta + inst), nu = __ldg(p.nu + inst), rho = __ldg(p.rho + inst);
   ub[0] = ub[1] = ub[2] = ub[3] = 0.0f;
@@ -63,7 +65,7 @@ __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile 
   if (T.kind == KIND_INT) {
     const float R = u[1] + beta * u[2] - nu * u[3] - rho * u[0] * (1.0f - u[0]);
     if (!p.grad) {
-      if (pt.act) {
+      if (pt.act && write) {
         const int64_t g = T.first + slot;
         if (p.u) p.u[g] = u[0];
         if (p.ut) p.ut[g] = u[1];
@@ -85,7 +87,7 @@ __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile 
   } else if (T.kind == KIND_IC) {
     const float B = u[0] - sinf(pt.x);
     if (!p.grad) {
-      if (pt.act && p.res_ic) p.res_ic[T.first + slot] = B;
+      if (pt.act && write && p.res_ic) p.res_ic[T.first + slot] = B;
       return false;
     }
     const float n = mse_count(p, inst, 1, p.ic_off);
@@ -95,10 +97,10 @@ __device__ __forceinline__ bool residual_and_seeds(const KParams &p, const Tile 
     if (!pt.act) { lp = 0.0f; gB = 0.0f; }
     ub[0] = gB;
   } else {
-    const float uo = __shfl_xor_sync(0xffffffffu, u[0], 1);
+    const float uo = __shfl_xor_sync(0xffffffffu, u[0], pair_xor);
     const float B = pt.side ? (uo - u[0]) : (u[0] - uo);
     if (!p.grad) {
-      if (pt.act && pt.side == 0 && p.res_bc) p.res_bc[T.first + (slot >> 1)] = B;
+      if (pt.act && write && pt.side == 0 && p.res_bc) p.res_bc[T.first + (slot >> 1)] = B;
       return false;
     }
     const float n = mse_count(p, inst, 2, p.bc_off);

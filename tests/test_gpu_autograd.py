@@ -66,9 +66,11 @@ def test_captured_spinprop_graph_equals_eager_steps(P):
 @pytest.mark.parametrize("form", ["fast", "full"])
 def test_autograd_gradient_matches_central_differences_of_the_kernel_loss(P, form):
     """The gradient behind lrnr_loss against central differences of lrnr_loss itself
-    (FP32 forward), along a random direction of s per instance: (L(s + h d) -
-    L(s - h d)) / 2h = <dL/ds, d> + O(h^2) + O(eps_FP32 L / h); with h = 2e-3 both error
-    terms are below 1e-4 of the derivative, held to 2e-3."""
+    (FP32 forward), along a random unit direction of s per instance: (L(s + h d) -
+    L(s - h d)) / 2h = <dL/ds, d> + O(h^2) + O(eps L / h).  With h = 5e-3 the truncation
+    term is about 1e-5 of the derivative and the rounding term, the loss's own FP32
+    error (a few 1e-7 of L, the parity tests) over h, about 1e-4 of L: held to
+    1e-3 |<dL/ds, d>| + 2e-4 L."""
     from paper_2410_04001_gb300.autograd import lrnr_loss
     g = synth.rng(8)
     net = synth.make_net(g, L=3, M=48, r=8)
@@ -78,13 +80,15 @@ def test_autograd_gradient_matches_central_differences_of_the_kernel_loss(P, for
     install_fast(P, model, rows, Xis)
     db = P.DeviceBatch.from_host(bt)
     s = db.s.clone().requires_grad_(True)
-    lrnr_loss(s, model, db, form=form).sum().backward()
+    lo = lrnr_loss(s, model, db, form=form)
+    lo.sum().backward()
     d = torch.tensor(g.standard_normal(tuple(s.shape)), dtype=torch.float32, device="cuda")
     d = d / d.norm(dim=1, keepdim=True)
-    h = 2e-3
+    h = 5e-3
     with torch.no_grad():
         lp = lrnr_loss((s + h * d).contiguous(), model, db, form=form).double()
         lm = lrnr_loss((s - h * d).contiguous(), model, db, form=form).double()
     fd = (lp - lm) / (2.0 * h)
     an = (s.grad.double() * d.double()).sum(dim=1)
-    assert torch.all((fd - an).abs() <= 2e-3 * an.abs().clamp_min(1e-3)), (fd, an)
+    tol = 1e-3 * an.abs() + 2e-4 * lo.detach().double().abs()
+    assert torch.all((fd - an).abs() <= tol), (fd, an, lo)
