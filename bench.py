@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
     ap.add_argument("--no-configs", action="store_true", help="skip the batched / SPInProp workloads")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="collective backend at N ranks (gloo: host-side all-reduce)")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one kernel case --steps times (for profilers) and exit")
     return ap.parse_args()
@@ -723,11 +725,17 @@ def main():
     import paper_2410_04001_gb300 as P
     import synth
 
+    # one rank per GPU; with fewer GPUs than ranks (a functional check of the N-rank
+    # path with the gloo backend) ranks share devices
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
 
     # N ranks: one instance with N x 69,632 points, each rank its block of every point
     # class, normalised by the whole instance's counts; one all-reduce of (loss, dL/ds)
@@ -992,13 +1000,14 @@ def main():
                                 "the instance's counts, all-reduce of loss and dL/ds, lrnr_adam_update)"),
                        "points_per_step": n_total,
                        "parallelism": f"points of one instance split over {world} ranks" if world > 1 else "single GPU",
-                       "l2": "flushed before every timed step (256 MiB write)", "cuda_graph": True},
+                       "l2": "flushed before every timed step (256 MiB write)", "cuda_graph": world == 1},
             "roofline": roof,
             "cpu_baseline": cpu_base,
             "e2e": {"value": n_total / (e2e_ms * 1e-3), "unit": "points/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "note": "one pinned host -> device copy of the batch arrays and s, spinprop_step, "
-                            "one copy of s and the loss back to host"},
+                    "note": ("one pinned host -> device copy of the batch arrays and s, "
+                             + ("spinprop_step" if world == 1 else "the sharded step") +
+                             ", one copy of s and the loss back to host")},
             # per SPInProp step at N = 1: the FastLRNR kernel (it computes its own tile
             # schedule for up to 4,096 instances) and the fixed-order reduction + Adam
             # kernel; at N ranks: the FastLRNR kernel, the reduction, the Adam update
