@@ -298,7 +298,9 @@ def run_cpu_baseline():
             "sample": (f"FP64 NumPy oracle, FastLRNR SPInProp step (residual + gradient + Adam) "
                        f"over the full 69,632-point batch, {d['steps']} steps in {d['seconds']:.1f} s; "
                        f"BLAS threads = {cores} (value_1_thread: the same with one BLAS thread, "
-                       f"{d1['steps'] if d1 else 0} steps)")}
+                       f"{d1['steps'] if d1 else 0} steps).  The oracle's step is a chain of small "
+                       f"NumPy operations, not BLAS-bound: it runs on one core in effect, and the "
+                       f"extra BLAS threads do not speed it up")}
 
 
 # --------------------------------------------------------------------------- reference arm

@@ -1,8 +1,10 @@
 """CUDA-graph capture of launch-bound loops (the SPInProp fast phase).
 
-A SPInProp step is three kernels; at the paper's fast-phase sizes (12 collocation
-points, a few thousand in batched use) the host launch cost dominates, so the
-whole loop of ``n_steps`` steps is captured once and replayed.
+A SPInProp step is one kernel (batches whose tiles fit in one round of the grid:
+the tile kernel also reduces the gradient and applies Adam) or two (the tile kernel,
+then the fixed-order reduction with Adam); at the paper's fast-phase sizes (12
+collocation points, a few thousand in batched use) the host launch cost dominates,
+so the whole loop of ``n_steps`` steps is captured once and replayed.
 """
 from __future__ import annotations
 
