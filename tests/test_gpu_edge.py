@@ -119,8 +119,10 @@ def test_unsupported_combinations_are_reported(P):
     net = synth.make_net(g, L=2, M=64, r=40)
     bt = synth.make_batch(g, net, 10, 2, 2, 1.0, 0.1, 0.1)
     model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
-    db = P.DeviceBatch.from_host(bt)
-    P.lrnr_residual_grad(model, "full", "fp32", db)
+    db = P.DeviceBatch.from_host(as_f32_batch(bt))
+    lo, ds, dbb = P.lrnr_residual_grad(model, "full", "fp32", db)
+    ro, rs, rb = lrnr64.residual_grad(net, as_f32_batch(bt), "full")
+    assert rel(ds.cpu(), rs) < 1e-5 and rel(dbb.cpu(), rb) < 1e-5 and rel(lo.cpu(), ro) < 1e-5
     for prec in ("tf32", "bf16x3"):
         with pytest.raises(P.LrnrError) as e:
             P.lrnr_residual_grad(model, "full", prec, db)
