@@ -504,6 +504,9 @@ __global__ void __launch_bounds__(128, MINB) k_fast(const __grid_constant__ KPar
       if (toff[i] == toff[i + 1]) fast_finish_instance(p, i, toff, red_s, wsum, kstep);
   }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the CTA's last tile: the kernel that reduces the partial rows may be scheduled
+    // now (it waits on the device for this grid to complete)
+    if (tile + (int)gridDim.x >= ntiles) asm volatile("griddepcontrol.launch_dependents;");
     const Tile T = decode_tile(p, tile, toff);
     __syncthreads();
     for (int j = tid; j < (L + 1) * RM; j += NT) {

@@ -7,6 +7,31 @@
 namespace lrnr {
 namespace {
 
+// The reduction kernels are launched as programmatic dependents of the tile kernel
+// before them (launch_dependent): they may start while its last tiles run, and wait
+// here, after any prologue that reads nothing the tile kernel writes, until it has
+// completed and its writes are visible.  Without the launch attribute this returns at
+// once.
+__device__ __forceinline__ void wait_prerequisite_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch `kernel` on `st` as a programmatic dependent of the kernel before it.
+template <typename Kern, typename... Args>
+cudaError_t launch_dependent(Kern kernel, dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // tile_off[i] = first tile of instance i (exclusive prefix sum); one block.  A batch
 // whose offsets fail offsets_ok gets no tiles (every offset zero) and DEV_BADBATCH.
 __global__ void __launch_bounds__(1024) k_tile_offsets(const __grid_constant__ KParams p,
@@ -94,6 +119,7 @@ __device__ __forceinline__ void scatter_out(const RedArgs &a, int i, int j, floa
 // grid (n_inst, ceil(n_needed / 32)), block (32, 32): x = entry, y = tile group.
 __global__ void __launch_bounds__(1024) k_reduce(const __grid_constant__ RedArgs a) {
   __shared__ float sh[32][33];
+  wait_prerequisite_grid();
   const int i = blockIdx.x;
   const int j = blockIdx.y * 32 + threadIdx.x;
   const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
@@ -132,6 +158,7 @@ __global__ void __launch_bounds__(256) k_reduce_adam2(const __grid_constant__ Ad
   __shared__ float loss_sh;
   __shared__ int last;
   const int i = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+  wait_prerequisite_grid();
   const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
   const int DB0 = 1 + (a.L + 1) * a.RM;
   float *grow = gsum + ((int64_t)i * kAdamGroups + g) * DB0;
@@ -226,9 +253,9 @@ __global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
   const int i = blockIdx.x / kClRed;
   const int crank = (int)cl.block_rank();
   const int tid = threadIdx.x, col = tid % COLS, ph = tid / COLS;
-  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
   const int DB0 = 1 + (a.L + 1) * a.RM;
-  // CTA 0 starts reading s, m, v (and the anchor) of its Adam entries now
+  // CTA 0 starts reading s, m, v (and the anchor) of its Adam entries now (the tile
+  // kernel before this one reads s and writes none of them)
   float sv = 0.0f, mv0 = 0.0f, vv0 = 0.0f, an = 0.0f;
   const int64_t o = (int64_t)i * a.sum_r + tid;
   const bool adam_lane = crank == 0 && tid < a.sum_r;
@@ -238,6 +265,8 @@ __global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
     vv0 = A.v[o];
     if (A.anchor) an = A.anchor[o];
   }
+  wait_prerequisite_grid();
+  const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
   float acc = 0.0f;
   if (col < DB0) {
     constexpr int STEP = kClRed * PH;             // distance between this thread's rows
@@ -317,6 +346,7 @@ __global__ void __cluster_dims__(kClRed, 1, 1) __launch_bounds__(kClThreads)
   const int crank = (int)cl.block_rank();
   const int tid = threadIdx.x, col = tid % COLS, ph = tid / COLS;
   const int j = blockIdx.y * COLS + col;
+  wait_prerequisite_grid();
   const int t0 = a.tile_off[i], t1 = a.tile_off[i + 1];
   float acc = 0.0f;
   if (j < a.n_needed) {
@@ -429,10 +459,11 @@ cudaError_t launch_reduce(const KParams &p, int n_needed, int form_fast, const i
   const int64_t blocks = ((int64_t)n_needed + 127) / 128;
   if ((int64_t)p.n_inst * kClRed * blocks <= 2 * (int64_t)num_sms) {
     // few instances: one cluster per (instance, 128 entries), one round of loads
-    k_reduce_cl<<<dim3(p.n_inst * kClRed, (unsigned)blocks), kClThreads, 0, st>>>(a);
+    return launch_dependent(k_reduce_cl, dim3(p.n_inst * kClRed, (unsigned)blocks), dim3(kClThreads),
+                            st, a);
   } else {
     dim3 grid(p.n_inst, (n_needed + 31) / 32), block(32, 32);
-    k_reduce<<<grid, block, 0, st>>>(a);
+    return launch_dependent(k_reduce, grid, block, st, a);
   }
   return cudaGetLastError();
 }
@@ -458,11 +489,11 @@ cudaError_t launch_reduce_adam(const KParams &p, float *s, float *m, float *v, c
   // many instances already give the two-level form enough parallelism
   if (p.sum_r <= kClThreads && DB0 <= 256 && (int64_t)p.n_inst * kClRed <= 2 * (int64_t)num_sms) {
     if (DB0 <= 128)
-      k_reduce_adam_cl<128><<<p.n_inst * kClRed, kClThreads, 0, st>>>(A);
+      return launch_dependent(k_reduce_adam_cl<128>, dim3(p.n_inst * kClRed), dim3(kClThreads), st, A);
     else
-      k_reduce_adam_cl<256><<<p.n_inst * kClRed, kClThreads, 0, st>>>(A);
+      return launch_dependent(k_reduce_adam_cl<256>, dim3(p.n_inst * kClRed), dim3(kClThreads), st, A);
   } else if (gsum && cnt) {
-    k_reduce_adam2<<<dim3(p.n_inst, kAdamGroups), 256, 0, st>>>(A, gsum, cnt);
+    return launch_dependent(k_reduce_adam2, dim3(p.n_inst, kAdamGroups), dim3(256), st, A, gsum, cnt);
   } else {
     return cudaErrorInvalidValue;   // the two-level form needs its group rows and tickets
   }
