@@ -90,9 +90,9 @@ typedef struct lrnr_model lrnr_model;
  * [off[i], off[i+1]) of each class.  Totals are host values and must equal
  * int_off[n_inst], ic_off[n_inst], bc_off[n_inst].  The kernels check the offsets
  * on the device: offsets that decrease, start below zero or end past the totals
- * make the call process no point (outputs zero; spinprop_step applies its Adam
- * update with a zero loss gradient) and record LRNR_EINVAL for
- * lrnr_last_device_status.
+ * make the call process no point (lrnr_residual writes no output; loss and
+ * gradients are zero; spinprop_step applies its Adam update with a zero loss
+ * gradient) and record LRNR_EINVAL for lrnr_last_device_status.
  *
  * norm (optional, device int64 [n_inst][3]): the denominators of the three MSE
  * means of Eq. 3.5 per instance (interior, initial, periodic), used in place of
