@@ -975,10 +975,19 @@ def main():
     hout = torch.zeros(out_hi - out_lo, dtype=torch.uint8).pin_memory()
     h2d, d2h = n_in, out_hi - out_lo
 
-    def e2e_step():
-        dbuf[:n_in].copy_(hbuf[:n_in], non_blocking=True)
-        step_on(db_e2e, dv["s"], dv["loss"])
-        hout.copy_(dbuf[out_lo:out_hi], non_blocking=True)
+    if world == 1:
+        # the package's captured step with its host transfers in the same graph: one
+        # replay = pinned host -> device copy, spinprop_step, device -> pinned host copy
+        from paper_2410_04001_gb300.graph import SpinpropGraph
+        ge2e = SpinpropGraph(model, db_e2e, dv["s"], m, v, step_ctr, 1, "fast", "fp32",
+                             loss_out=dv["loss"], copy_in=[(dbuf[:n_in], hbuf[:n_in])],
+                             copy_out=[(hout, dbuf[out_lo:out_hi])], lr=1e-3)
+        e2e_step = ge2e.replay
+    else:
+        def e2e_step():
+            dbuf[:n_in].copy_(hbuf[:n_in], non_blocking=True)
+            step_on(db_e2e, dv["s"], dv["loss"])
+            hout.copy_(dbuf[out_lo:out_hi], non_blocking=True)
 
     for _ in range(3):
         e2e_step()
@@ -1009,7 +1018,9 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "note": ("one pinned host -> device copy of the batch arrays and s, "
                              + ("spinprop_step" if world == 1 else "the sharded step") +
-                             ", one copy of s and the loss back to host")},
+                             ", one copy of s and the loss back to host" +
+                             (" (all three in one captured SpinpropGraph replay)" if world == 1
+                              else ""))},
             # per SPInProp step at N = 1: the FastLRNR kernel (it computes its own tile
             # schedule for up to 4,096 instances) and the fixed-order reduction + Adam
             # kernel; at N ranks: the FastLRNR kernel, the reduction, the Adam update

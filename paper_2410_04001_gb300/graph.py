@@ -15,22 +15,35 @@ from . import binding as B
 
 class SpinpropGraph:
     """Captured ``spinprop_step(..., n_steps)``; ``replay()`` runs the steps again
-    on the same device buffers (s, Adam moments, step counter, loss)."""
+    on the same device buffers (s, Adam moments, step counter, loss).
+
+    ``copy_in`` / ``copy_out``: optional ``(dst, src)`` tensor pairs copied before /
+    after the steps inside the same graph, e.g. a batch staged in pinned host memory
+    going to the device buffers the batch views, and ``s`` and the loss coming back
+    to pinned host memory, so that one replay is a whole host-to-host step."""
 
     def __init__(self, model, batch, s, m, v, step, n_steps=1, form="fast", prec="fp32",
-                 loss_out=None, **adam):
+                 loss_out=None, copy_in=(), copy_out=(), **adam):
         B.lrnr_reserve(model, batch.n_points, batch.n_inst)
         self.args = (model, form, prec, batch, s, m, v, step)
         self.kw = dict(n_steps=n_steps, loss_out=loss_out, **adam)
+        self.copy_in, self.copy_out = tuple(copy_in), tuple(copy_out)
         stream = torch.cuda.Stream()
         stream.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(stream):          # warm-up outside the graph
-            B.spinprop_step(*self.args, **self.kw)
+            self._body()
         torch.cuda.current_stream().wait_stream(stream)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
-            B.spinprop_step(*self.args, **self.kw)
+            self._body()
+
+    def _body(self):
+        for dst, src in self.copy_in:
+            dst.copy_(src, non_blocking=True)
+        B.spinprop_step(*self.args, **self.kw)
+        for dst, src in self.copy_out:
+            dst.copy_(src, non_blocking=True)
 
     def replay(self):
         self.graph.replay()

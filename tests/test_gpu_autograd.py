@@ -63,6 +63,44 @@ def test_captured_spinprop_graph_equals_eager_steps(P):
     assert torch.equal(s1, s2) and torch.equal(m1, m2) and torch.equal(v1, v2)
 
 
+def test_captured_step_with_host_transfers(P):
+    """SpinpropGraph with copy_in / copy_out: each replay takes s from pinned host
+    memory, runs the step and returns s and the loss to pinned host memory.  Feeding
+    every replay the s that the previous one returned reproduces the eager steps bit
+    for bit, and the host copies hold the device results."""
+    from paper_2410_04001_gb300.graph import SpinpropGraph
+    g = synth.rng(7)
+    net = synth.make_net(g, L=3, M=32, r=8)
+    bt = as_f32_batch(synth.make_instances(g, net, 3, 200, 400))
+    rows, Xis, _ = eim_for(net, bt.s[0], 16)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    install_fast(P, model, rows, Xis)
+    db = P.DeviceBatch.from_host(bt)
+    dev = torch.device("cuda")
+
+    def state():
+        s = db.s.clone()
+        return s, torch.zeros_like(s), torch.zeros_like(s), torch.zeros(1, dtype=torch.int64, device=dev)
+    s1, m1, v1, k1 = state()
+    lo1 = torch.zeros(db.n_inst, dtype=torch.float32, device=dev)
+    for _ in range(4):
+        P.spinprop_step(model, "fast", "fp32", db, s1, m1, v1, k1, 1, lr=1e-2, loss_out=lo1)
+    s2, m2, v2, k2 = state()
+    lo2 = torch.zeros_like(lo1)
+    h_in = db.s.detach().cpu().pin_memory()
+    h_s, h_lo = torch.zeros_like(h_in).pin_memory(), torch.zeros(db.n_inst).pin_memory()
+    gr = SpinpropGraph(model, db.with_s(s2), s2, m2, v2, k2, 1, loss_out=lo2,
+                       copy_in=[(s2, h_in)], copy_out=[(h_s, s2), (h_lo, lo2)], lr=1e-2)
+    torch.cuda.synchronize()                 # the warm-up ran the first step
+    for _ in range(3):
+        h_in.copy_(h_s)                      # the host hands the returned s back in
+        gr.replay()
+        torch.cuda.synchronize()
+    assert k1.item() == 4 and k2.item() == 4
+    assert torch.equal(s1.cpu(), h_s) and torch.equal(lo1.cpu(), h_lo)
+    assert torch.equal(s1, s2) and torch.equal(m1, m2) and torch.equal(v1, v2)
+
+
 @pytest.mark.parametrize("form", ["fast", "full"])
 def test_autograd_gradient_matches_central_differences_of_the_kernel_loss(P, form):
     """The gradient behind lrnr_loss against central differences of lrnr_loss itself
