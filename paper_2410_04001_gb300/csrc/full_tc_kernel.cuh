@@ -86,18 +86,24 @@ struct TcLayout {
   static constexpr int PARTS = PREC == 3 ? 3 : 1;   // pieces of each operand
   static constexpr int A1B = TNT * RM * ES;         // one (channel, piece) rank-r operand
   static constexpr int A24B = TNT * NC * ES;        // one (channel, piece) width operand
-  static constexpr bool A24_TMEM = PREC == 3;       // chunk activations in tensor memory
+  static constexpr bool SPLIT = PREC == 3;
+  // chunk activations (the A operand of GEMM2 / GEMM4) in tensor memory: split-BF16
+  // (three pieces), and BF16 in 32-column chunks up to rank 32 (one piece), where the
+  // epilogue's hand-over through tcgen05.st costs less than stores to shared memory
+  // and the proxy fence they need
+  static constexpr bool A24_TMEM = SPLIT || (PREC == 1 && NC == 32 && RM <= 32);
+  static constexpr int APIECES = SPLIT ? 3 : 1;     // pieces of a TMEM activation
   static constexpr int BBYTES = PREC == 3 ? Pk<RM, NC>::ALL : Pk<RM, NC, ES>::HI;
   static constexpr int OFF_A1 = 0;
   static constexpr int OFF_A3 = OFF_A1 + 4 * PARTS * A1B;
   static constexpr int OFF_A24 = OFF_A3 + 4 * PARTS * A1B;
   static constexpr int OFF_B = OFF_A24 + (A24_TMEM ? 0 : 4 * A24B);
-  // tensor-memory columns: D1 [4][NC], D3 [4][NC], D24 [4][RM], then (split-BF16) the
-  // chunk activations [4 channels][3 pieces][NC/2] (two BF16 per column) and the
-  // running sum R24 [4][RM] of the chunks' rank-r results
+  // tensor-memory columns: D1 [4][NC], D3 [4][NC], D24 [4][RM], then the chunk
+  // activations [4 channels][APIECES pieces][NC/2] (two BF16 per column) and
+  // (split-BF16) the running sum R24 [4][RM] of the chunks' rank-r results
   static constexpr int TM_A24 = 8 * NC + 4 * RM;
-  static constexpr int TM_R24 = TM_A24 + 6 * NC;
-  static constexpr int TM_END = A24_TMEM ? TM_R24 + 4 * RM : TM_A24;
+  static constexpr int TM_R24 = TM_A24 + 2 * APIECES * NC;
+  static constexpr int TM_END = SPLIT ? TM_R24 + 4 * RM : (A24_TMEM ? TM_R24 : TM_A24);
   static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
   static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
   static constexpr int OFF_F = OFF_B + NB * BSTRIDE;
@@ -213,24 +219,37 @@ __device__ __forceinline__ void mma_split_t(uint32_t d, uint32_t aT, uint32_t aC
 }
 
 // Write n consecutive chunk-activation values of channel c (this thread's row, K
-// positions k0..k0+n-1 of the chunk, k0 even) to the tensor-memory A operand of
-// split-BF16: three pieces, two BF16 per column.  n = 16 or 8.
-template <int NC, int n>
+// positions k0..k0+n-1 of the chunk, k0 even) to the tensor-memory A operand of GEMM2 /
+// GEMM4, two BF16 per column: PIECES = 3, the three pieces of split-BF16 (piece i at
+// HALF * i columns further); PIECES = 1, BF16 rounded to nearest even like the
+// shared-memory operand.  n = 16 or 8.
+template <int NC, int n, int PIECES>
 __device__ __forceinline__ void put_act_tmem(uint32_t ta_row, int c, int k0, const float *v) {
   constexpr int HALF = NC / 2;           // columns per (channel, piece)
-  uint32_t h[n / 2], m[n / 2], l[n / 2];
+  const uint32_t col = ta_row + (uint32_t)(PIECES * c * HALF + k0 / 2);
+  if constexpr (PIECES == 3) {
+    uint32_t h[n / 2], m[n / 2], l[n / 2];
 #pragma unroll
-  for (int i = 0; i < n / 2; ++i) tc::split3_bf16x2(v[2 * i], v[2 * i + 1], h[i], m[i], l[i]);
-  const uint32_t col = ta_row + (uint32_t)(3 * c * HALF + k0 / 2);
-  if constexpr (n == 16) {
-    tc::tmem_st8(col, h);
-    tc::tmem_st8(col + HALF, m);
-    tc::tmem_st8(col + 2 * HALF, l);
+    for (int i = 0; i < n / 2; ++i) tc::split3_bf16x2(v[2 * i], v[2 * i + 1], h[i], m[i], l[i]);
+    if constexpr (n == 16) {
+      tc::tmem_st8(col, h);
+      tc::tmem_st8(col + HALF, m);
+      tc::tmem_st8(col + 2 * HALF, l);
+    } else {
+      static_assert(n == 8, "activation group");
+      tc::tmem_st4(col, h);
+      tc::tmem_st4(col + HALF, m);
+      tc::tmem_st4(col + 2 * HALF, l);
+    }
   } else {
-    static_assert(n == 8, "activation group");
-    tc::tmem_st4(col, h);
-    tc::tmem_st4(col + HALF, m);
-    tc::tmem_st4(col + 2 * HALF, l);
+    uint32_t h[n / 2];
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      h[i] = *reinterpret_cast<const uint32_t *>(&b);
+    }
+    if constexpr (n == 16) tc::tmem_st8(col, h);
+    else tc::tmem_st4(col, h);
   }
 }
 
@@ -283,7 +302,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   const uint32_t sA1u = tc::smem_u32(sA1), sA3u = tc::smem_u32(sA3), sA24u = tc::smem_u32(sA24);
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const uint32_t D1 = tb, D3 = tb + 4 * NC, D24 = tb + 8 * NC;
-  const uint32_t TA = tb + Lay::TM_A24;   // split-BF16 chunk activations (A of GEMM2 / GEMM4)
+  const uint32_t TA = tb + Lay::TM_A24;   // chunk activations in TMEM (A of GEMM2 / GEMM4)
   const uint32_t R24 = tb + Lay::TM_R24;  // split-BF16 running sum of the chunks' GEMM2 / GEMM4
   constexpr uint32_t ID_W = PREC == 2 ? tc::idesc_tf32(128, NC) : tc::idesc_bf16(128, NC);
   constexpr uint32_t ID_R = PREC == 2 ? tc::idesc_tf32(128, RM) : tc::idesc_bf16(128, RM);
@@ -308,7 +327,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     for (int k0 = 0; k0 < RM; k0 += 16) {
       float w[16];
       tc::tmem_ld16(D24 + lane_base + c * RM + k0, w);
-      if (Lay::A24_TMEM && NCH > 1) {
+      if (Lay::SPLIT && NCH > 1) {
         float r[16];
         tc::tmem_ld16(R24 + lane_base + c * RM + k0, r);
         tc::tmem_ld_wait();
@@ -382,7 +401,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     for (int j = 0; j < NCH; ++j) {
       const int n = n0 + j;
       if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }   // GEMM2(j-1) done
-      if constexpr (Lay::A24_TMEM) if (j > 0) fold_chunk(j == 1);
+      if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
       if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
       if (!wait_b(n)) { dead = true; return; }
       if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
@@ -424,7 +443,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         }
         if constexpr (Lay::A24_TMEM) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC>(TA + lane_base, c, c0, a[c]);
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, Lay::APIECES>(TA + lane_base, c, c0, a[c]);
           tc::tmem_st_wait();
         } else {
 #pragma unroll
@@ -447,9 +466,13 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < NC / KPM; ++kk) {
-            if constexpr (Lay::A24_TMEM)
+            if constexpr (Lay::SPLIT)
               mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
                                   sB + 3 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
+            else if constexpr (Lay::A24_TMEM)
+              tc::mma_bf16_ts(D24 + c * RM, TA + c * (NC / 2) + kk * 8,
+                              tc::sdesc(sB + 3 * PK::T + kk * 256, 128, SBO_W), ID_R,
+                              (j > 0 || kk > 0) ? 1u : 0u);
             else
               mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
                                       sB + 3 * PK::T + kk * 256, SBO_W, SBO_W, ID_R,
@@ -534,7 +557,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     for (int j = 0; j < NCH; ++j) {
       const int n = n0 + j;
       if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
-      if constexpr (Lay::A24_TMEM) if (j > 0) fold_chunk(j == 1);
+      if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
       if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
       if (!wait_b(n)) { dead = true; return; }
       if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
@@ -584,7 +607,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         }
         if constexpr (Lay::A24_TMEM) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) put_act_tmem<NC, 8>(TA + lane_base, c, c0, wb[c]);
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, 8, Lay::APIECES>(TA + lane_base, c, c0, wb[c]);
         } else {
 #pragma unroll
           for (int c = 0; c < C; ++c) put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0, NC, wb[c]);
@@ -605,9 +628,13 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int kk = 0; kk < NC / KPM; ++kk) {
-            if constexpr (Lay::A24_TMEM)
+            if constexpr (Lay::SPLIT)
               mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
                                   sB + 2 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
+            else if constexpr (Lay::A24_TMEM)
+              tc::mma_bf16_ts(D24 + c * RM, TA + c * (NC / 2) + kk * 8,
+                              tc::sdesc(sB + 2 * PK::T + kk * 256, 128, SBO_W), ID_R,
+                              (j > 0 || kk > 0) ? 1u : 0u);
             else
               mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
                                       sB + 2 * PK::T + kk * 256, SBO_W, SBO_W, ID_R,
