@@ -63,7 +63,12 @@ PROFILE_CASES = {
     "fast_fp32_cdr": "FastLRNR SPInProp step, FP32 (k_fast + reduction / Adam), CDR M=256 r=16 L=5, 69,632 points",
     "fastk_fp32_paper_d2": "FastLRNR SPInProp step, FP32 reduced coordinates (k_fastk), M=4000 r=(1,49,30,25,1) "
                            "rhat=5, 65,536 + 2,048 + 1,024 pairs",
+    "fast_bf16_cdr": "FastLRNR SPInProp step, reduced network on BF16 tensor cores (k_full_tc), CDR M=256 "
+                     "r=16 L=5, 69,632 points",
+    "fast_tf32_cdr": "FastLRNR SPInProp step, reduced network on TF32 tensor cores (k_full_tc), CDR M=256 "
+                     "r=16 L=5, 69,632 points",
     "full_bf16_cdr": "full-width residual + gradient, BF16 tensor cores (k_full_tc), CDR M=256 r=16 L=5",
+    "full_tf32_cdr": "full-width residual + gradient, TF32 tensor cores (k_full_tc), CDR M=256 r=16 L=5",
     "full_bf16x3_cdr": "full-width residual + gradient, split-BF16 tensor cores (k_full_tc), CDR M=256 r=16 L=5",
     "full_fp32_cdr": "full-width residual + gradient, FP32 SIMT (k_full_fp32), CDR M=256 r=16 L=5",
     "full_fp32_stress": "full-width residual + gradient, FP32 SIMT at rank 32 (k_full_fp32_sl, two threads "
@@ -103,7 +108,8 @@ def run_profile_case(args):
         s = db.s.clone()
         m, v = torch.zeros_like(s), torch.zeros_like(s)
         k = torch.zeros(1, dtype=torch.int64, device=dev)
-        fn = lambda: P.spinprop_step(model, "fast", "fp32", db, s, m, v, k, 1, lr=1e-3)
+        fprec = case.split("_")[1]
+        fn = lambda: P.spinprop_step(model, "fast", fprec, db, s, m, v, k, 1, lr=1e-3)
     elif case == "full_fp32_paper_d2":
         s = db.s.clone()
         m, v = torch.zeros_like(s), torch.zeros_like(s)

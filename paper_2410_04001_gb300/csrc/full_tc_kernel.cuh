@@ -87,22 +87,24 @@ struct TcLayout {
   static constexpr int A1B = TNT * RM * ES;         // one (channel, piece) rank-r operand
   static constexpr int A24B = TNT * NC * ES;        // one (channel, piece) width operand
   static constexpr bool SPLIT = PREC == 3;
-  // chunk activations (the A operand of GEMM2 / GEMM4) in tensor memory: split-BF16
-  // (three pieces), and BF16 in 32-column chunks up to rank 32 (one piece), where the
-  // epilogue's hand-over through tcgen05.st costs less than stores to shared memory
-  // and the proxy fence they need
-  static constexpr bool A24_TMEM = SPLIT || (PREC == 1 && NC == 32 && RM <= 32);
-  static constexpr int APIECES = SPLIT ? 3 : 1;     // pieces of a TMEM activation
+  // tensor-memory columns of one channel's chunk activation: three BF16 pieces of NC/2
+  // columns (two BF16 per column), one such piece, or NC TF32 columns
+  static constexpr int ACOLS = SPLIT ? 3 * (NC / 2) : (PREC == 2 ? NC : NC / 2);
+  static constexpr int TM_A24 = 8 * NC + 4 * RM;
+  // chunk activations (the A operand of GEMM2 / GEMM4) in tensor memory wherever they
+  // fit beside the accumulators (always for split-BF16, whose pieces would not fit in
+  // shared memory): the epilogue's hand-over through tcgen05.st costs less than stores
+  // to shared memory and the proxy fence they need
+  static constexpr bool A24_TMEM = SPLIT || TM_A24 + 4 * ACOLS <= tmem_cols<NC, RM, PREC>();
   static constexpr int BBYTES = PREC == 3 ? Pk<RM, NC>::ALL : Pk<RM, NC, ES>::HI;
   static constexpr int OFF_A1 = 0;
   static constexpr int OFF_A3 = OFF_A1 + 4 * PARTS * A1B;
   static constexpr int OFF_A24 = OFF_A3 + 4 * PARTS * A1B;
   static constexpr int OFF_B = OFF_A24 + (A24_TMEM ? 0 : 4 * A24B);
   // tensor-memory columns: D1 [4][NC], D3 [4][NC], D24 [4][RM], then the chunk
-  // activations [4 channels][APIECES pieces][NC/2] (two BF16 per column) and
-  // (split-BF16) the running sum R24 [4][RM] of the chunks' rank-r results
-  static constexpr int TM_A24 = 8 * NC + 4 * RM;
-  static constexpr int TM_R24 = TM_A24 + 2 * APIECES * NC;
+  // activations [4 channels][ACOLS] and (split-BF16) the running sum R24 [4][RM] of the
+  // chunks' rank-r results
+  static constexpr int TM_R24 = TM_A24 + 4 * ACOLS;
   static constexpr int TM_END = SPLIT ? TM_R24 + 4 * RM : (A24_TMEM ? TM_R24 : TM_A24);
   static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
   static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
@@ -220,12 +222,25 @@ __device__ __forceinline__ void mma_split_t(uint32_t d, uint32_t aT, uint32_t aC
 
 // Write n consecutive chunk-activation values of channel c (this thread's row, K
 // positions k0..k0+n-1 of the chunk, k0 even) to the tensor-memory A operand of GEMM2 /
-// GEMM4, two BF16 per column: PIECES = 3, the three pieces of split-BF16 (piece i at
-// HALF * i columns further); PIECES = 1, BF16 rounded to nearest even like the
-// shared-memory operand.  n = 16 or 8.
-template <int NC, int n, int PIECES>
+// GEMM4.  Split-BF16 (PREC 3): the three BF16 pieces, two per column, piece i at
+// NC/2 * i columns further; BF16 (PREC 1): one piece, rounded to nearest even like
+// the shared-memory operand; TF32 (PREC 2): one element per column, rounded to nearest
+// (ties away) like the shared-memory operand.  n = 16 or 8.
+template <int NC, int n, int PREC>
 __device__ __forceinline__ void put_act_tmem(uint32_t ta_row, int c, int k0, const float *v) {
   constexpr int HALF = NC / 2;           // columns per (channel, piece)
+  if constexpr (PREC == 2) {
+    const uint32_t col = ta_row + (uint32_t)(c * NC + k0);
+#pragma unroll
+    for (int g = 0; g < n; g += 8) {
+      uint32_t w[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(v[g + i]));
+      tc::tmem_st8(col + g, w);
+    }
+    return;
+  }
+  constexpr int PIECES = PREC == 3 ? 3 : 1;
   const uint32_t col = ta_row + (uint32_t)(PIECES * c * HALF + k0 / 2);
   if constexpr (PIECES == 3) {
     uint32_t h[n / 2], m[n / 2], l[n / 2];
@@ -443,7 +458,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         }
         if constexpr (Lay::A24_TMEM) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, Lay::APIECES>(TA + lane_base, c, c0, a[c]);
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, PREC>(TA + lane_base, c, c0, a[c]);
           tc::tmem_st_wait();
         } else {
 #pragma unroll
@@ -469,8 +484,12 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
             if constexpr (Lay::SPLIT)
               mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
                                   sB + 3 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
+            else if constexpr (Lay::A24_TMEM && PREC == 2)
+              tc::mma_tf32_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
+                              tc::sdesc(sB + 3 * PK::T + kk * 256, 128, SBO_W), ID_R,
+                              (j > 0 || kk > 0) ? 1u : 0u);
             else if constexpr (Lay::A24_TMEM)
-              tc::mma_bf16_ts(D24 + c * RM, TA + c * (NC / 2) + kk * 8,
+              tc::mma_bf16_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
                               tc::sdesc(sB + 3 * PK::T + kk * 256, 128, SBO_W), ID_R,
                               (j > 0 || kk > 0) ? 1u : 0u);
             else
@@ -607,7 +626,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         }
         if constexpr (Lay::A24_TMEM) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) put_act_tmem<NC, 8, Lay::APIECES>(TA + lane_base, c, c0, wb[c]);
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, 8, PREC>(TA + lane_base, c, c0, wb[c]);
         } else {
 #pragma unroll
           for (int c = 0; c < C; ++c) put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0, NC, wb[c]);
@@ -631,8 +650,12 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
             if constexpr (Lay::SPLIT)
               mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
                                   sB + 2 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
+            else if constexpr (Lay::A24_TMEM && PREC == 2)
+              tc::mma_tf32_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
+                              tc::sdesc(sB + 2 * PK::T + kk * 256, 128, SBO_W), ID_R,
+                              (j > 0 || kk > 0) ? 1u : 0u);
             else if constexpr (Lay::A24_TMEM)
-              tc::mma_bf16_ts(D24 + c * RM, TA + c * (NC / 2) + kk * 8,
+              tc::mma_bf16_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
                               tc::sdesc(sB + 2 * PK::T + kk * 256, 128, SBO_W), ID_R,
                               (j > 0 || kk > 0) ? 1u : 0u);
             else
