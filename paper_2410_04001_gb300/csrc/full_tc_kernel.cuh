@@ -109,6 +109,11 @@ struct TcLayout {
   static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
   static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
   static constexpr int OFF_F = OFF_B + NB * BSTRIDE;
+  // MMA issue order: GEMM1 of the next chunk right behind GEMM2 of this one (needs two B
+  // buffers); chosen for the 32-column full-width kernels and split-BF16, whose layers
+  // have several chunks, and not for the reduced network's 16-column chunks (one chunk
+  // per layer at rhat = 16, where it measured slower)
+  static constexpr bool B2B = NB >= 2 && (NC == 32 || SPLIT);
   // float area: s [(L+1)*RM], red [4][PL] (loss, dL/ds, output-bias dL/db), dbw [8][HC];
   // then the mbarriers and the TMEM base address
   static __host__ __device__ int floats(int L) { return (L + 1) * RM + 4 * (2 + (L + 1) * RM) + 8 * HC; }
@@ -398,6 +403,133 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
     return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], ctl.pb[n % Lay::NB], p);
   };
 
+  // MMA issue (thread 0) for the chunk whose bases are in B buffer n
+  auto issue_g1 = [&](int n) {   // forward GEMM1: a_c = (s q_c) U_chunk^T into D1
+    const uint32_t sB = tc::smem_u32(bbuf(n));
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int kk = 0; kk < RM / KPM; ++kk)
+        mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
+  };
+  // GEMM2 (forward, rank-r tile at 3T) or GEMM4 (reverse, at 2T) of chunk j of the
+  // layer: the chunk activations times the tile, into D24 (split-BF16 afresh per chunk)
+  auto issue_g24 = [&](int n, int j, int toff) {
+    const uint32_t sB = tc::smem_u32(bbuf(n)) + (uint32_t)toff;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int kk = 0; kk < NC / KPM; ++kk) {
+        if constexpr (Lay::SPLIT)
+          mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
+                              sB + kk * 256, SBO_W, ID_R, kk > 0);
+        else if constexpr (Lay::A24_TMEM && PREC == 2)
+          tc::mma_tf32_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
+                          tc::sdesc(sB + kk * 256, 128, SBO_W), ID_R, (j > 0 || kk > 0) ? 1u : 0u);
+        else if constexpr (Lay::A24_TMEM)
+          tc::mma_bf16_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
+                          tc::sdesc(sB + kk * 256, 128, SBO_W), ID_R, (j > 0 || kk > 0) ? 1u : 0u);
+        else
+          mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
+                                  sB + kk * 256, SBO_W, SBO_W, ID_R, (j > 0 || kk > 0));
+      }
+  };
+  auto fwd_epilogue = [&](int n) {
+    const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
+    {
+      const int c0 = half * HC;
+      float a[C][HC];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if constexpr (HC == 16) tc::tmem_ld16(D1 + lane_base + c * NC + c0, a[c]);
+        else tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
+      }
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < HC; ++i) {
+        float z, d1, d2;
+        act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
+        if constexpr (C == 4) {
+          a[3][i] = d2 * a[2][i] * a[2][i] + d1 * a[3][i];
+          a[1][i] *= d1;
+          a[2][i] *= d1;
+        }
+        a[0][i] = z;
+      }
+      if constexpr (Lay::A24_TMEM) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, PREC>(TA + lane_base, c, c0, a[c]);
+        tc::tmem_st_wait();
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int h = 0; h < HC / 8; ++h) {
+            float w8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
+            put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0 + h * 8, NC, w8);
+          }
+      }
+    }
+  };
+
+  auto issue_g13 = [&](int n) {   // reverse GEMM1 into D1 and GEMM3 into D3
+    const uint32_t sB = tc::smem_u32(bbuf(n));
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int kk = 0; kk < RM / KPM; ++kk) {
+        mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
+        mma_split<RM, PREC, NC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+                                Lay::A1B, sB + PK::T + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
+      }
+  };
+  auto rev_epilogue = [&](int n) {
+    const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
+#pragma unroll
+    for (int h8 = 0; h8 < HC / 8; ++h8) {
+      const int c0 = half * HC + h8 * 8;
+      float a[C][8], wb[C][8];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
+        tc::tmem_ld8(D3 + lane_base + c * NC + c0, wb[c]);
+      }
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float z, d1, d2;
+        act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
+        float ab0 = wb[0][i] * d1;
+        if constexpr (C == 4) {
+          const float d3 = d1 * (6.0f * z * z - 2.0f);
+          ab0 += d2 * (wb[1][i] * a[1][i] + wb[2][i] * a[2][i]) +
+                 wb[3][i] * (d3 * a[2][i] * a[2][i] + d2 * a[3][i]);
+          wb[2][i] = wb[2][i] * d1 + 2.0f * wb[3][i] * d2 * a[2][i];
+          wb[3][i] = wb[3][i] * d1;
+          wb[1][i] = wb[1][i] * d1;
+        }
+        wb[0][i] = ab0;
+      }
+      if constexpr (Lay::A24_TMEM) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) put_act_tmem<NC, 8, PREC>(TA + lane_base, c, c0, wb[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0, NC, wb[c]);
+      }
+      float g8[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) g8[i] = wb[0][i];
+      const float r = warp_reduce_scatter<8>(g8);
+      if ((lane & 3) == 0) dbw[warp * HC + h8 * 8 + (lane >> 2)] = r;
+    }
+    if constexpr (Lay::A24_TMEM) tc::tmem_st_wait();
+  };
+
   // ---------------- forward (the operand A1 of layer l >= 1 is written at the end
   // of layer l - 1, from its rank-r result)
   if (lead) {
@@ -412,94 +544,83 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   for (int l = 0; l < L && !dead; ++l) {
     const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
     const int n0 = ctl.chunk_ctr;
-    fetch(lp, 0, n0);
-    for (int j = 0; j < NCH; ++j) {
-      const int n = n0 + j;
-      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }   // GEMM2(j-1) done
-      if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
-      if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
-      if (!wait_b(n)) { dead = true; return; }
-      if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
-      const uint32_t sB = tc::smem_u32(bbuf(n));
+    if constexpr (Lay::B2B) {
+      // GEMM1 of chunk j + 1 is issued right behind GEMM2 of chunk j, under one commit
+      // (the tensor core runs them in order), so that a chunk waits for one MMA
+      // completion, not two; B(j + 1) is requested once the wait for GEMM1(j) has
+      // shown GEMM2(j - 1), the last reader of its buffer, complete
+      fetch(lp, 0, n0);
+      if (NCH > 1) fetch(lp, 1, n0 + 1);
+      if (!wait_b(n0)) { dead = true; return; }
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc::fence_after_sync();
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int kk = 0; kk < RM / KPM; ++kk)
-            mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
-                                    Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
+        issue_g1(n0);
         tc::mma_commit(ctl.b1);
       }
       ctl.p1 = true;
-      if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
-      const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
-      {
-        const int c0 = half * HC;
-        float a[C][HC];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          if constexpr (HC == 16) tc::tmem_ld16(D1 + lane_base + c * NC + c0, a[c]);
-          else tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
+      for (int j = 0; j < NCH; ++j) {
+        const int n = n0 + j;
+        // GEMM1(j) done, and with it GEMM2(j - 1)
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+        if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
+        if (j >= 1 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+        fwd_epilogue(n);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue_g24(n, j, 3 * PK::T);
         }
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < HC; ++i) {
-          float z, d1, d2;
-          act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
-          if constexpr (C == 4) {
-            a[3][i] = d2 * a[2][i] * a[2][i] + d1 * a[3][i];
-            a[1][i] *= d1;
-            a[2][i] *= d1;
+        if (j + 1 < NCH) {
+          if (!wait_b(n + 1)) {
+            // GEMM2(j) is in flight: commit it for the drain
+            if (tid == 0) tc::mma_commit(ctl.b2);
+            ctl.p2 = true;
+            dead = true;
+            return;
           }
-          a[0][i] = z;
-        }
-        if constexpr (Lay::A24_TMEM) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, PREC>(TA + lane_base, c, c0, a[c]);
-          tc::tmem_st_wait();
+          if (tid == 0) {
+            issue_g1(n + 1);
+            tc::mma_commit(ctl.b1);
+          }
+          ctl.p1 = true;
         } else {
-#pragma unroll
-          for (int c = 0; c < C; ++c)
-#pragma unroll
-            for (int h = 0; h < HC / 8; ++h) {
-              float w8[8];
-#pragma unroll
-              for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
-              put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0 + h * 8, NC, w8);
-            }
+          if (tid == 0) tc::mma_commit(ctl.b2);
+          ctl.p2 = true;
         }
       }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int kk = 0; kk < NC / KPM; ++kk) {
-            if constexpr (Lay::SPLIT)
-              mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
-                                  sB + 3 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
-            else if constexpr (Lay::A24_TMEM && PREC == 2)
-              tc::mma_tf32_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
-                              tc::sdesc(sB + 3 * PK::T + kk * 256, 128, SBO_W), ID_R,
-                              (j > 0 || kk > 0) ? 1u : 0u);
-            else if constexpr (Lay::A24_TMEM)
-              tc::mma_bf16_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
-                              tc::sdesc(sB + 3 * PK::T + kk * 256, 128, SBO_W), ID_R,
-                              (j > 0 || kk > 0) ? 1u : 0u);
-            else
-              mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
-                                      sB + 3 * PK::T + kk * 256, SBO_W, SBO_W, ID_R,
-                                      (j > 0 || kk > 0));
-          }
-        tc::mma_commit(ctl.b2);
+    } else {
+      fetch(lp, 0, n0);
+      for (int j = 0; j < NCH; ++j) {
+        const int n = n0 + j;
+        if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }   // GEMM2(j-1) done
+        if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
+        if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
+        if (!wait_b(n)) { dead = true; return; }
+        if (Lay::NB >= 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue_g1(n);
+          tc::mma_commit(ctl.b1);
+        }
+        ctl.p1 = true;
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+        fwd_epilogue(n);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue_g24(n, j, 3 * PK::T);
+          tc::mma_commit(ctl.b2);
+        }
+        ctl.p2 = true;
       }
-      ctl.p2 = true;
     }
     ctl.chunk_ctr = n0 + NCH;
     if (!wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
@@ -572,107 +693,96 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       }
     }
     const int n0 = ctl.chunk_ctr;
-    fetch(lp, 0, n0);
-    for (int j = 0; j < NCH; ++j) {
-      const int n = n0 + j;
-      if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
-      if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
-      if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
-      if (!wait_b(n)) { dead = true; return; }
-      if (Lay::NB == 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
-      const uint32_t sB = tc::smem_u32(bbuf(n));
+    if constexpr (Lay::B2B) {
+      // as in the forward sweep: GEMM1 / GEMM3 of chunk j + 1 right behind GEMM4 of
+      // chunk j, one commit for both
+      fetch(lp, 0, n0);
+      if (NCH > 1) fetch(lp, 1, n0 + 1);
+      if (!wait_b(n0)) { dead = true; return; }
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc::fence_after_sync();
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int kk = 0; kk < RM / KPM; ++kk) {
-            mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
-                                    Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
-            mma_split<RM, PREC, NC>(D3 + c * NC, sA3u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
-                                    Lay::A1B, sB + PK::T + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
-          }
+        issue_g13(n0);
         tc::mma_commit(ctl.b1);
       }
       ctl.p1 = true;
-      if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
-      const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
-#pragma unroll
-      for (int h8 = 0; h8 < HC / 8; ++h8) {
-        const int c0 = half * HC + h8 * 8;
-        float a[C][8], wb[C][8];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
-          tc::tmem_ld8(D3 + lane_base + c * NC + c0, wb[c]);
+      for (int j = 0; j < NCH; ++j) {
+        const int n = n0 + j;
+        // GEMM1 / GEMM3 (j) done, and with them GEMM4(j - 1)
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+        if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
+        if (j >= 1 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+        rev_epilogue(n);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue_g24(n, j, 2 * PK::T);
         }
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float z, d1, d2;
-          act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
-          float ab0 = wb[0][i] * d1;
-          if constexpr (C == 4) {
-            const float d3 = d1 * (6.0f * z * z - 2.0f);
-            ab0 += d2 * (wb[1][i] * a[1][i] + wb[2][i] * a[2][i]) +
-                   wb[3][i] * (d3 * a[2][i] * a[2][i] + d2 * a[3][i]);
-            wb[2][i] = wb[2][i] * d1 + 2.0f * wb[3][i] * d2 * a[2][i];
-            wb[3][i] = wb[3][i] * d1;
-            wb[1][i] = wb[1][i] * d1;
+        if (tid < NC) {
+          // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
+          const int h = tid / HC, cc = tid % HC;
+          const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
+                          dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
+          const int col = j * NC + tid;
+          if (col < M) prow[DB0 + l * M + col] = v;
+        }
+        if (j + 1 < NCH) {
+          if (!wait_b(n + 1)) {
+            // GEMM4(j) is in flight: commit it for the drain
+            if (tid == 0) tc::mma_commit(ctl.b2);
+            ctl.p2 = true;
+            dead = true;
+            return;
           }
-          wb[0][i] = ab0;
-        }
-        if constexpr (Lay::A24_TMEM) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) put_act_tmem<NC, 8, PREC>(TA + lane_base, c, c0, wb[c]);
+          if (tid == 0) {
+            issue_g13(n + 1);
+            tc::mma_commit(ctl.b1);
+          }
+          ctl.p1 = true;
         } else {
-#pragma unroll
-          for (int c = 0; c < C; ++c) put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0, NC, wb[c]);
+          if (tid == 0) tc::mma_commit(ctl.b2);
+          ctl.p2 = true;
         }
-        float g8[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) g8[i] = wb[0][i];
-        const float r = warp_reduce_scatter<8>(g8);
-        if ((lane & 3) == 0) dbw[warp * HC + h8 * 8 + (lane >> 2)] = r;
       }
-      if constexpr (Lay::A24_TMEM) tc::tmem_st_wait();
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-#pragma unroll
-          for (int kk = 0; kk < NC / KPM; ++kk) {
-            if constexpr (Lay::SPLIT)
-              mma_split_t<RM, NC>(D24 + c * RM, TA + 3 * c * (NC / 2) + kk * 8, NC / 2,
-                                  sB + 2 * PK::T + kk * 256, SBO_W, ID_R, kk > 0);
-            else if constexpr (Lay::A24_TMEM && PREC == 2)
-              tc::mma_tf32_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
-                              tc::sdesc(sB + 2 * PK::T + kk * 256, 128, SBO_W), ID_R,
-                              (j > 0 || kk > 0) ? 1u : 0u);
-            else if constexpr (Lay::A24_TMEM)
-              tc::mma_bf16_ts(D24 + c * RM, TA + c * Lay::ACOLS + kk * 8,
-                              tc::sdesc(sB + 2 * PK::T + kk * 256, 128, SBO_W), ID_R,
-                              (j > 0 || kk > 0) ? 1u : 0u);
-            else
-              mma_split<RM, PREC, NC>(D24 + c * RM, sA24u + c * Lay::A24B + kk * 256, Lay::A24B,
-                                      sB + 2 * PK::T + kk * 256, SBO_W, SBO_W, ID_R,
-                                      (j > 0 || kk > 0));
-          }
-        tc::mma_commit(ctl.b2);
-      }
-      ctl.p2 = true;
-      if (tid < NC) {
-        // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
-        const int h = tid / HC, cc = tid % HC;
-        const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
-                        dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
-        const int col = j * NC + tid;
-        if (col < M) prow[DB0 + l * M + col] = v;
+    } else {
+      fetch(lp, 0, n0);
+      for (int j = 0; j < NCH; ++j) {
+        const int n = n0 + j;
+        if (j > 0 && !wait_bar(ctl.b2, ctl.ph2, ctl.p2, p)) { dead = true; return; }
+        if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
+        if (Lay::NB == 1 && j > 0) fetch(lp, j, n);
+        if (!wait_b(n)) { dead = true; return; }
+        if (Lay::NB >= 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue_g13(n);
+          tc::mma_commit(ctl.b1);
+        }
+        ctl.p1 = true;
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+        rev_epilogue(n);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue_g24(n, j, 2 * PK::T);
+          tc::mma_commit(ctl.b2);
+        }
+        ctl.p2 = true;
+        if (tid < NC) {
+          // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
+          const int h = tid / HC, cc = tid % HC;
+          const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
+                          dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
+          const int col = j * NC + tid;
+          if (col < M) prow[DB0 + l * M + col] = v;
+        }
       }
     }
     ctl.chunk_ctr = n0 + NCH;
