@@ -306,6 +306,13 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   const int row = tid & (TNT - 1);       // point / TMEM lane
   const int half = tid >> 7;             // column half of the epilogue
   const bool lead = tid < TNT;           // threads doing the per-point work
+  // MMA issuers: lane 0 of warps 0-3, one per jet channel; each issues its channel's
+  // MMAs (so that every accumulator's MMAs come from one thread, in order) and commits
+  // them, so that the issue is spread over four warps; the MMA barriers count four
+  // commits, and an issuer without a channel (tiles of one channel) commits nothing
+  // pending, which arrives at once
+  const bool issuer = (tid & 31) == 0 && warp < 4;
+  const int ic = warp;                   // the issuer's channel
   const int L = p.L, M = p.M;
   const int NCH = (M + NC - 1) / NC;
   unsigned char *sA1 = sm + Lay::OFF_A1;
@@ -406,8 +413,8 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   // MMA issue (thread 0) for the chunk whose bases are in B buffer n
   auto issue_g1 = [&](int n) {   // forward GEMM1: a_c = (s q_c) U_chunk^T into D1
     const uint32_t sB = tc::smem_u32(bbuf(n));
-#pragma unroll
-    for (int c = 0; c < C; ++c)
+    const int c = ic;
+    if (c < C)
 #pragma unroll
       for (int kk = 0; kk < RM / KPM; ++kk)
         mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
@@ -417,8 +424,8 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   // layer: the chunk activations times the tile, into D24 (split-BF16 afresh per chunk)
   auto issue_g24 = [&](int n, int j, int toff) {
     const uint32_t sB = tc::smem_u32(bbuf(n)) + (uint32_t)toff;
-#pragma unroll
-    for (int c = 0; c < C; ++c)
+    const int c = ic;
+    if (c < C)
 #pragma unroll
       for (int kk = 0; kk < NC / KPM; ++kk) {
         if constexpr (Lay::SPLIT)
@@ -477,8 +484,8 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
 
   auto issue_g13 = [&](int n) {   // reverse GEMM1 into D1 and GEMM3 into D3
     const uint32_t sB = tc::smem_u32(bbuf(n));
-#pragma unroll
-    for (int c = 0; c < C; ++c)
+    const int c = ic;
+    if (c < C)
 #pragma unroll
       for (int kk = 0; kk < RM / KPM; ++kk) {
         mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
@@ -554,7 +561,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       if (!wait_b(n0)) { dead = true; return; }
       tc::fence_async_smem();
       __syncthreads();
-      if (tid == 0) {
+      if (issuer) {
         tc::fence_after_sync();
         issue_g1(n0);
         tc::mma_commit(ctl.b1);
@@ -570,25 +577,25 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
           tc::fence_after_sync();
           issue_g24(n, j, 3 * PK::T);
         }
         if (j + 1 < NCH) {
           if (!wait_b(n + 1)) {
             // GEMM2(j) is in flight: commit it for the drain
-            if (tid == 0) tc::mma_commit(ctl.b2);
+            if (issuer) tc::mma_commit(ctl.b2);
             ctl.p2 = true;
             dead = true;
             return;
           }
-          if (tid == 0) {
+          if (issuer) {
             issue_g1(n + 1);
             tc::mma_commit(ctl.b1);
           }
           ctl.p1 = true;
         } else {
-          if (tid == 0) tc::mma_commit(ctl.b2);
+          if (issuer) tc::mma_commit(ctl.b2);
           ctl.p2 = true;
         }
       }
@@ -603,7 +610,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         if (Lay::NB >= 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
         tc::fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
           tc::fence_after_sync();
           issue_g1(n);
           tc::mma_commit(ctl.b1);
@@ -614,7 +621,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
           tc::fence_after_sync();
           issue_g24(n, j, 3 * PK::T);
           tc::mma_commit(ctl.b2);
@@ -701,7 +708,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
       if (!wait_b(n0)) { dead = true; return; }
       tc::fence_async_smem();
       __syncthreads();
-      if (tid == 0) {
+      if (issuer) {
         tc::fence_after_sync();
         issue_g13(n0);
         tc::mma_commit(ctl.b1);
@@ -717,7 +724,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
           tc::fence_after_sync();
           issue_g24(n, j, 2 * PK::T);
         }
@@ -732,18 +739,18 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         if (j + 1 < NCH) {
           if (!wait_b(n + 1)) {
             // GEMM4(j) is in flight: commit it for the drain
-            if (tid == 0) tc::mma_commit(ctl.b2);
+            if (issuer) tc::mma_commit(ctl.b2);
             ctl.p2 = true;
             dead = true;
             return;
           }
-          if (tid == 0) {
+          if (issuer) {
             issue_g13(n + 1);
             tc::mma_commit(ctl.b1);
           }
           ctl.p1 = true;
         } else {
-          if (tid == 0) tc::mma_commit(ctl.b2);
+          if (issuer) tc::mma_commit(ctl.b2);
           ctl.p2 = true;
         }
       }
@@ -758,7 +765,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         if (Lay::NB >= 2 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
         tc::fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
           tc::fence_after_sync();
           issue_g13(n);
           tc::mma_commit(ctl.b1);
@@ -769,7 +776,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (issuer) {
           tc::fence_after_sync();
           issue_g24(n, j, 2 * PK::T);
           tc::mma_commit(ctl.b2);
@@ -824,7 +831,8 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM, PREC>() == 256) ? 2 : 
   uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
   if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC, RM, PREC>());
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
+    // b1, b2: one commit per MMA issuer; the B-buffer barriers: one arrival (expect_tx)
+    for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], i < 2 ? 4u : 1u);
     tc::fence_mbar_init();
   }
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
