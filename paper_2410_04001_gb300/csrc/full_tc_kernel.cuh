@@ -107,13 +107,21 @@ struct TcLayout {
   static constexpr int TM_R24 = TM_A24 + 4 * ACOLS;
   static constexpr int TM_END = SPLIT ? TM_R24 + 4 * RM : (A24_TMEM ? TM_R24 : TM_A24);
   static constexpr int BSTRIDE = (BBYTES + 127) & ~127;
-  static constexpr int NB = OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1;  // B buffers
+  // B buffers: four for the pipelined forward sweep where they fit (TF32 32-column and
+  // split-BF16 kernels: chosen by measurement, the BF16 kernel ran 2 % slower with it),
+  // else two, else one
+  static constexpr bool NB4 = ((NC == 32 && PREC == 2) || SPLIT) &&
+                              OFF_B + 4 * BSTRIDE + 16 * 1024 <= 227 * 1024;
+  static constexpr int NB = NB4 ? 4 : (OFF_B + 2 * BSTRIDE + 16 * 1024 <= 227 * 1024 ? 2 : 1);
   static constexpr int OFF_F = OFF_B + NB * BSTRIDE;
   // MMA issue order: GEMM1 of the next chunk right behind GEMM2 of this one (needs two B
   // buffers); chosen for the 32-column full-width kernels and split-BF16, whose layers
   // have several chunks, and not for the reduced network's 16-column chunks (one chunk
   // per layer at rhat = 16, where it measured slower)
   static constexpr bool B2B = NB >= 2 && (NC == 32 || SPLIT);
+  // forward sweep pipelined: GEMM1 of chunk j + 1 (into D3 and D1 in turn; D3 is free in
+  // the forward sweep) runs during the epilogue of chunk j
+  static constexpr bool PIPE = NB == 4;
   // float area: s [(L+1)*RM], red [4][PL] (loss, dL/ds, output-bias dL/db), dbw [8][HC];
   // then the mbarriers and the TMEM base address
   static __host__ __device__ int floats(int L) { return (L + 1) * RM + 4 * (2 + (L + 1) * RM) + 8 * HC; }
@@ -134,6 +142,21 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, bool &pend
   if (!all && threadIdx.x == 0) set_status(p.status, DEV_TIMEOUT);
   tc::fence_after_sync();
   return all;
+}
+
+// One thread's own bounded wait, without a CTA barrier, for a completion that only
+// this thread's next steps depend on; the CTA agrees on a failure at its next barrier
+// (the caller passes the result there).
+__device__ __forceinline__ bool wait_own(uint64_t *bar, uint32_t &ph, bool &pend, const KParams &p) {
+  const bool ok = tc::mbar_wait(bar, ph, p.max_wait);
+  if (ok) {
+    ph ^= 1u;
+    pend = false;
+  } else {
+    set_status(p.status, DEV_TIMEOUT);
+  }
+  tc::fence_after_sync();
+  return ok;
 }
 
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -287,11 +310,11 @@ __device__ __forceinline__ void act_jet(float a0, float &z, float &d1, float &d2
 
 struct Ctl {
   uint64_t *b1, *b2, *bb;   // GEMM barriers, B-buffer barriers [NB]
-  uint32_t ph1, ph2, phb[2];
+  uint32_t ph1, ph2, phb[4];
   int chunk_ctr;            // chunks consumed so far (selects the B buffer)
   // an MMA commit or a copy is outstanding on the barrier (uniform over the CTA): the
   // drain after a timeout waits for exactly these
-  bool p1, p2, pb[2];
+  bool p1, p2, pb[4];
 };
 
 template <int RM, int PREC, int C, int NC>
@@ -411,15 +434,17 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   };
 
   // MMA issue (thread 0) for the chunk whose bases are in B buffer n
-  auto issue_g1 = [&](int n) {   // forward GEMM1: a_c = (s q_c) U_chunk^T into D1
+  // forward GEMM1: a_c = (s q_c) U_chunk^T into the accumulator at column D
+  auto issue_g1d = [&](int n, uint32_t D) {
     const uint32_t sB = tc::smem_u32(bbuf(n));
     const int c = ic;
     if (c < C)
 #pragma unroll
       for (int kk = 0; kk < RM / KPM; ++kk)
-        mma_split<RM, PREC, NC>(D1 + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
+        mma_split<RM, PREC, NC>(D + c * NC, sA1u + (Lay::PARTS * c) * Lay::A1B + kk * 256,
                                 Lay::A1B, sB + kk * 256, SBO_R, SBO_R, ID_W, kk > 0);
   };
+  auto issue_g1 = [&](int n) { issue_g1d(n, D1); };
   // GEMM2 (forward, rank-r tile at 3T) or GEMM4 (reverse, at 2T) of chunk j of the
   // layer: the chunk activations times the tile, into D24 (split-BF16 afresh per chunk)
   auto issue_g24 = [&](int n, int j, int toff) {
@@ -551,7 +576,90 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   for (int l = 0; l < L && !dead; ++l) {
     const unsigned char *lp = pack + (size_t)l * NCH * PK::CHUNK;
     const int n0 = ctl.chunk_ctr;
-    if constexpr (Lay::B2B) {
+    if constexpr (Lay::PIPE) {
+      // GEMM1 of chunk j + 1 is issued, into the other of D1 / D3, as soon as GEMM1 of
+      // chunk j is done, so that it runs during the epilogue of chunk j; GEMM2 of chunk
+      // j - 1 runs then too, and the epilogue waits for it only before it overwrites the
+      // chunk activations.  B(j + 2) goes into the buffer of chunk j - 2, whose MMAs the
+      // wait for GEMM1(j) covers (each issuer's commit covers its earlier MMAs)
+      auto dacc = [&](int j) { return (j & 1) ? D3 : D1; };
+      fetch(lp, 0, n0);
+      if (NCH > 1) fetch(lp, 1, n0 + 1);
+      if (!wait_b(n0)) { dead = true; return; }
+      tc::fence_async_smem();
+      __syncthreads();
+      if (issuer) {
+        tc::fence_after_sync();
+        issue_g1d(n0, D1);
+        tc::mma_commit(ctl.b1);
+      }
+      ctl.p1 = true;
+      for (int j = 0; j < NCH; ++j) {
+        const int n = n0 + j;
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }   // GEMM1(j) done
+        if (j + 2 < NCH) fetch(lp, j + 2, n + 2);
+        if (j + 1 < NCH) {
+          if (!wait_b(n + 1)) { dead = true; return; }
+          if (issuer) {
+            issue_g1d(n + 1, dacc(j + 1));
+            tc::mma_commit(ctl.b1);
+          }
+          ctl.p1 = true;
+        }
+        const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
+        const uint32_t Dj = dacc(j);
+        const int c0 = half * HC;
+        float a[C][HC];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          if constexpr (HC == 16) tc::tmem_ld16(Dj + lane_base + c * NC + c0, a[c]);
+          else tc::tmem_ld8(Dj + lane_base + c * NC + c0, a[c]);
+        }
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < HC; ++i) {
+          float z, d1, d2;
+          act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
+          if constexpr (C == 4) {
+            a[3][i] = d2 * a[2][i] * a[2][i] + d1 * a[3][i];
+            a[1][i] *= d1;
+            a[2][i] *= d1;
+          }
+          a[0][i] = z;
+        }
+        bool own_ok = true;
+        if (j > 0) {
+          // GEMM2(j - 1) has read the activations (split-BF16: its result is folded);
+          // each thread waits for itself, the CTA agrees at the barrier below
+          own_ok = wait_own(ctl.b2, ctl.ph2, ctl.p2, p);
+          if constexpr (Lay::SPLIT) fold_chunk(j == 1);
+        }
+        if constexpr (Lay::A24_TMEM) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, PREC>(TA + lane_base, c, c0, a[c]);
+          tc::tmem_st_wait();
+        } else {
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int h = 0; h < HC / 8; ++h) {
+              float w8[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) w8[i] = a[c][h * 8 + i];
+              put8<PREC>(sA24 + c * Lay::A24B, Lay::A24B, row, c0 + h * 8, NC, w8);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        if (__syncthreads_or(!own_ok)) { dead = true; return; }
+        if (issuer) {
+          tc::fence_after_sync();
+          issue_g24(n, j, 3 * PK::T);
+          tc::mma_commit(ctl.b2);
+        }
+        ctl.p2 = true;
+      }
+    } else if constexpr (Lay::B2B) {
       // GEMM1 of chunk j + 1 is issued right behind GEMM2 of chunk j, under one commit
       // (the tensor core runs them in order), so that a chunk waits for one MMA
       // completion, not two; B(j + 1) is requested once the wait for GEMM1(j) has
@@ -828,11 +936,11 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM, PREC>() == 256) ? 2 : 
   const int PL = 2 + (L + 1) * RM;
   float *red_s = fa + (L + 1) * RM;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + ((Lay::OFF_F + Lay::floats(L) * 4 + 15) & ~15));
-  uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 4);
+  uint32_t *tbase = reinterpret_cast<uint32_t *>(bar + 2 + Lay::NB);
   if (tid < 32) tc::tmem_alloc(tbase, tmem_cols<NC, RM, PREC>());
   if (tid == 0) {
     // b1, b2: one commit per MMA issuer; the B-buffer barriers: one arrival (expect_tx)
-    for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], i < 2 ? 4u : 1u);
+    for (int i = 0; i < 2 + Lay::NB; ++i) tc::mbar_init(&bar[i], i < 2 ? 4u : 1u);
     tc::fence_mbar_init();
   }
   if (p.step && blockIdx.x == 0 && tid == 0) atomicAdd((unsigned long long *)p.step, 1ull);
@@ -840,7 +948,8 @@ __global__ void __launch_bounds__(NTH, (tmem_cols<NC, RM, PREC>() == 256) ? 2 : 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tb = *tbase;
-  Ctl ctl{&bar[0], &bar[1], &bar[2], 0u, 0u, {0u, 0u}, 0, false, false, {false, false}};
+  Ctl ctl{&bar[0], &bar[1], &bar[2], 0u, 0u, {0u, 0u, 0u, 0u}, 0, false, false,
+          {false, false, false, false}};
   bool dead = false;
   float *qst = p.scratch + (size_t)blockIdx.x * (size_t)(L > 1 ? L - 1 : 1) * 4 * RM * TNT;
   const int ntiles = __ldg(p.tile_off + p.n_inst);
