@@ -604,6 +604,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
             issue_g1d(n + 1, dacc(j + 1));
             tc::mma_commit(ctl.b1);
           }
+          __syncwarp();   // the warp reconverges before the tensor-memory loads below
           ctl.p1 = true;
         }
         const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
