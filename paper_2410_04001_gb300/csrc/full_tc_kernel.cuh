@@ -28,13 +28,18 @@
 // memory and half the K of a BF16 MMA, so twice the MMAs per contraction.
 //
 // Eight warps: warps w and w+4 share TMEM lanes 32(w%4).. and split each chunk's
-// epilogue columns; warps 0-3 also do the per-point work.  Thread 0 issues the
-// MMAs and the bulk copies.  The bases are packed chunk by chunk in the operand
-// layout (no-swizzle K-major core matrices) so that one cp.async.bulk moves a
-// chunk; chunk j+1 is copied while chunk j is processed (two buffers when shared
-// memory allows).  The rank-r layer inputs q (FP32) are kept in a per-CTA global
-// scratch area (it stays in L2) for the reverse sweep.  Every mbarrier wait is
-// bounded.
+// epilogue columns; warps 0-3 also do the per-point work.  Lane 0 of warps 0-3
+// issues the MMAs of jet channel 0-3 (and commits them), thread 0 the bulk copies.
+// Where the chunk activations fit in TMEM beside the accumulators they go to GEMM2 /
+// GEMM4 from there (tcgen05.st), else through shared memory.  In the multi-chunk
+// kernels GEMM1 (GEMM1 + GEMM3) of chunk j+1 is issued right behind GEMM2 (GEMM4) of
+// chunk j under one commit; in the TF32 and split-BF16 forward sweep it is issued
+// earlier still, into D3 and D1 in turn, so that it runs during the epilogue of chunk
+// j.  The bases are packed chunk by chunk in the operand layout (no-swizzle K-major
+// core matrices) so that one cp.async.bulk moves a chunk; later chunks are copied
+// while earlier ones are processed (two or four buffers where shared memory allows).
+// The rank-r layer inputs q (FP32) are kept in a per-CTA global scratch area (it stays
+// in L2) for the reverse sweep.  Every mbarrier wait is bounded.
 #pragma once
 
 #include <cuda_bf16.h>
