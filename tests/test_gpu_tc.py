@@ -59,6 +59,24 @@ def test_tc_gradient_matches_oracle(P, prec, shape):
     assert P.lrnr_last_device_status(model) == 0
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3"])
+@pytest.mark.parametrize("shape", [(2, 32, 16), (3, 20, 8), (1, 32, 16), (2, 16, 16)])
+def test_tc_single_chunk_layers(P, prec, shape):
+    """Widths of one chunk (32 columns in BF16 / TF32, 16 in split-BF16; M = 20 a ragged
+    one) and a single hidden layer: the chunk loops without a next chunk to issue or
+    prefetch.  Loss, dL/ds and dL/db against the oracle."""
+    L, M, r = shape
+    net, bt = cdr_case(L=L, M=M, r=r, n=(300, 40, 20), seed=100 + L * M + r)
+    model = P.lrnr_build(net.L, net.M, net.r, net.U, net.V, net.b)
+    db = P.DeviceBatch.from_host(bt)
+    lo, ds, dbb = P.lrnr_residual_grad(model, "full", prec, db)
+    ro, rs, rb = lrnr64.residual_grad(net, bt, "full")
+    assert rel(lo.cpu(), ro) < TOL[prec]
+    assert rel(ds.cpu(), rs) < TOL[prec], rel(ds.cpu(), rs)
+    assert rel(dbb.cpu(), rb) < TOL[prec], rel(dbb.cpu(), rb)
+    assert P.lrnr_last_device_status(model) == 0
+
+
 def test_tc_ragged_instances(P):
     g = synth.rng(17)
     net = synth.make_net(g, L=3, M=64, r=16)
