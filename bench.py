@@ -991,9 +991,9 @@ def main():
         e2e_step = ge2e.replay
     else:
         def e2e_step():
-            dbuf[:n_in].copy_(hbuf[:n_in], non_blocking=True)
+            P.lrnr_copy_pinned(dbuf[:n_in], hbuf[:n_in])
             step_on(db_e2e, dv["s"], dv["loss"])
-            hout.copy_(dbuf[out_lo:out_hi], non_blocking=True)
+            P.lrnr_copy_pinned(hout, dbuf[out_lo:out_hi])
 
     for _ in range(3):
         e2e_step()
@@ -1024,7 +1024,8 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "note": ("one pinned host -> device copy of the batch arrays and s, "
                              + ("spinprop_step" if world == 1 else "the sharded step") +
-                             ", one copy of s and the loss back to host" +
+                             ", one copy of s and the loss back to host (both copies by the "
+                             "library's copy kernel, lrnr_copy_pinned)" +
                              (" (all three in one captured SpinpropGraph replay)" if world == 1
                               else ""))},
             # per SPInProp step at N = 1: the FastLRNR kernel (it computes its own tile

@@ -301,6 +301,25 @@ lrnr_status lrnr_adam_update(int32_t n_inst, int32_t sum_r, const float *grad, f
                              float beta2, float eps, float lambda_loc, const float *s_anchor,
                              const float *loss_in, float *loss_out, void *stream);
 
+/*
+ * lrnr_copy_pinned -- copy `bytes` bytes from `src` to `dst` with a kernel on `stream`
+ * that reads and writes through the unified address space (not an operation of the
+ * paper: it carries a step's batch and s in from the host and s and the loss back out,
+ * in less time than a copy-engine transfer at these sizes, and is captured into a CUDA
+ * graph like any launch).
+ *   dst, src : each either device memory of the current device (or managed memory) or
+ *              page-locked host memory (cudaHostAlloc / cudaMallocHost /
+ *              cudaHostRegister, e.g. a pinned torch tensor); any byte alignment
+ *              (16-byte loads where both addresses agree modulo 16).  Host bytes are
+ *              read uncached, so host writes made before the launch are seen.
+ *   The ranges must not overlap.  The caller owns both buffers and keeps them alive
+ *   until the copy has run; host results are complete once `stream` has been
+ *   synchronised.  bytes = 0 does nothing.
+ * Errors: LRNR_EINVAL for a null pointer with bytes > 0, pageable host memory, memory
+ * of another device, or overlapping ranges; LRNR_ECUDA if the launch fails.
+ */
+lrnr_status lrnr_copy_pinned(void *dst, const void *src, size_t bytes, void *stream);
+
 /* lrnr_reserve -- size the workspace for batches of up to max_points collocation
  * points (interior + initial + 2 x pairs) in up to max_inst instances.  Call it
  * before capturing a CUDA graph. */

@@ -10,4 +10,4 @@ from .binding import (DeviceBatch, LrnrError, Model, fastlrnr_select_rows, lrnr_
                       lrnr_residual, lrnr_residual_grad, lrnr_snapshots, lrnr_status_string,
                       lrnr_residual_grad_noalloc, lrnr_set_tuning, lrnr_timing, lrnr_timing_read, spinprop_step,
                       lrnr_measure_peaks, lrnr_set_wait_limit, lrnr_pod, lrnr_deim_rows,
-                      fastlrnr_select_rows_deim, lrnr_adam_update)
+                      fastlrnr_select_rows_deim, lrnr_adam_update, lrnr_copy_pinned)

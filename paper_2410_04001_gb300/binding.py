@@ -63,6 +63,7 @@ _SIGS = {
     "lrnr_adam_update": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P,
                                         ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
+    "lrnr_copy_pinned": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "lrnr_reserve": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "lrnr_model_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "lrnr_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -432,3 +433,20 @@ def lrnr_adam_update(grad, s, m, v, step, lr: float = 1e-3, beta1: float = 0.9,
                                 _ptr(s_anchor), _ptr(loss_in), _ptr(loss_out), _stream(stream))
     _check(rc, "lrnr_adam_update")
     return s
+
+
+def lrnr_copy_pinned(dst, src, stream=None):
+    """Copy tensor ``src`` into ``dst`` (same number of bytes, both contiguous) with the
+    library's copy kernel; each side is a CUDA tensor of the current device or a pinned
+    CPU tensor.  Stream-ordered: a CPU destination holds the result once the stream has
+    been synchronised."""
+    nb = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nb:
+        raise ValueError("lrnr_copy_pinned: dst and src differ in size")
+    if nb == 0:
+        return dst
+    for t in (dst, src):
+        if t.device.type == "cpu" and not t.is_pinned():
+            raise ValueError("lrnr_copy_pinned: CPU tensors must be pinned")
+    _check(lib().lrnr_copy_pinned(_ptr(dst), _ptr(src), nb, _stream(stream)), "lrnr_copy_pinned")
+    return dst

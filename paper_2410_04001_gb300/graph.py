@@ -20,7 +20,10 @@ class SpinpropGraph:
     ``copy_in`` / ``copy_out``: optional ``(dst, src)`` tensor pairs copied before /
     after the steps inside the same graph, e.g. a batch staged in pinned host memory
     going to the device buffers the batch views, and ``s`` and the loss coming back
-    to pinned host memory, so that one replay is a whole host-to-host step."""
+    to pinned host memory, so that one replay is a whole host-to-host step.  Each pair
+    is copied by the library's copy kernel (``lrnr_copy_pinned``: loads and stores
+    through the unified address space, host bytes read uncached), so a replay sees
+    what the host wrote to a pinned source before it."""
 
     def __init__(self, model, batch, s, m, v, step, n_steps=1, form="fast", prec="fp32",
                  loss_out=None, copy_in=(), copy_out=(), **adam):
@@ -40,10 +43,10 @@ class SpinpropGraph:
 
     def _body(self):
         for dst, src in self.copy_in:
-            dst.copy_(src, non_blocking=True)
+            B.lrnr_copy_pinned(dst, src)
         B.spinprop_step(*self.args, **self.kw)
         for dst, src in self.copy_out:
-            dst.copy_(src, non_blocking=True)
+            B.lrnr_copy_pinned(dst, src)
 
     def replay(self):
         self.graph.replay()
