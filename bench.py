@@ -186,7 +186,9 @@ class ClockSampler:
     """nvidia-smi samples of the SM clock and throttle reasons while the timed region
     runs.  Every GPU nvidia-smi lists is sampled (no --id: its id forms differ between
     driver versions); stop() keeps the lines of the GPU whose UUID torch reports, or
-    all lines when nvidia-smi lists a single GPU."""
+    all lines when nvidia-smi lists a single GPU.  start() returns once the first
+    sample has arrived (nvidia-smi takes a while to start), and stop() keeps the
+    samples that arrived between the two calls (the latest earlier ones if none did)."""
     QUERY = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -200,20 +202,25 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"],
+                 "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t_end = time.perf_counter() + 10.0
+            while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.t_start = time.perf_counter()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_stop = time.perf_counter()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -222,7 +229,10 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        rows = [[x.strip() for x in ln.split(",")] for ln in self.lines]
+        inside = [ln for ts, ln in self.lines if self.t_start <= ts <= t_stop]
+        if not inside:
+            inside = [ln for ts, ln in self.lines if ts < self.t_start][-8:]   # one line per GPU
+        rows = [[x.strip() for x in ln.split(",")] for ln in inside]
         rows = [f for f in rows if len(f) >= 9]
         uuids = {f[0].lower().replace("gpu-", "") for f in rows}
         if self.uuid in uuids:

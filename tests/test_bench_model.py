@@ -30,3 +30,29 @@ def test_flops_per_point_of_the_benchmark_network():
 def test_fp32_peak_from_unit_counts():
     # 152 SMs x 128 FP32 lanes x 2 flops x 2,070 MHz
     assert abs(bench.fp32_peak_tflops(2070.0) - 80.54784) < 1e-9
+
+
+def test_clock_sampler_keeps_our_gpu_and_the_timed_region(tmp_path, monkeypatch):
+    """ClockSampler against a stand-in nvidia-smi that prints two GPUs every 20 ms
+    (the first lines after a 0.2 s start-up): stop() reports only the samples of the
+    UUID it was given that arrived between start() and stop(), and the throttle
+    reasons marked Active in them."""
+    import os
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!/bin/sh\nsleep 0.2\n"
+        "while true; do\n"
+        "echo 'GPU-aaaa, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Active'\n"
+        "echo 'GPU-bbbb, 1500, 2070, 300.0, 0x0, Active, Not Active, Not Active, Not Active'\n"
+        "sleep 0.02\ndone\n")
+    os.chmod(fake, 0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    cs = bench.ClockSampler("GPU-AAAA")
+    cs.start()
+    assert cs.lines, "start() returns after the first sample"
+    time.sleep(0.3)
+    res = cs.stop()
+    assert res["sm_mhz"] == 2070.0 and res["sm_max_mhz"] == 2070.0
+    assert res["reasons"] == ["sw_power_cap"]
+    assert res["samples"] >= 3
