@@ -801,10 +801,14 @@ def main():
     def spin():
         step_on(db_s, s, loss_out)
 
-    # CUDA graph of one step (2 kernels).  Kernel timing: every 8th timed step runs the
+    # CUDA graph of one step (2 kernels).  Kernel timing: every EVERY-th timed step runs the
     # same step eagerly with the library's timing events around the FastLRNR kernel;
     # all events are read once, after the timed region, so that the host never waits
-    # for the GPU inside it (the host enqueues ahead and the GPU never idles).
+    # for the GPU inside it (the host enqueues ahead and the GPU never idles).  Such a
+    # step takes ~6 us longer than a replay (the events stand between the FastLRNR
+    # kernel and the reduction it would otherwise overlap), so only every 32nd carries
+    # them; the line reports both kinds of step (step_kinds).
+    EVERY = 32
     for _ in range(3):
         spin()
     torch.cuda.synchronize()
@@ -818,7 +822,7 @@ def main():
 
     def replay():
         step_counter[0] += 1
-        if graph is None or step_counter[0] % 8 == 1:
+        if graph is None or step_counter[0] % EVERY == 1:
             spin()
         else:
             graph.replay()
@@ -866,6 +870,13 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     ms_step = sum(per_step) / len(per_step)
+    # the two kinds of timed step at N = 1: graph replays, and the eager steps that
+    # carry the kernel-timing events (every EVERY-th, the first included)
+    ev_steps = per_step[::EVERY]
+    gr_steps = [t for i, t in enumerate(per_step) if i % EVERY]
+    step_kinds = {"graph_replay_ms": sum(gr_steps) / len(gr_steps) if gr_steps else None,
+                  "eager_with_kernel_events_ms": sum(ev_steps) / len(ev_steps),
+                  "eager_steps": len(ev_steps)} if graph is not None else None
     if dist:
         tt = torch.tensor([ms_step], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -1045,6 +1056,7 @@ def main():
             "gpu_launches": (2 if world == 1 else 4) * args.steps,
             "clocks": clk,
             "wall_s_timed_region": t_wall,
+            "step_kinds": step_kinds,
             "device_status": status,
             "variants": variants,
         }
