@@ -301,15 +301,48 @@ __device__ __forceinline__ void put_act_tmem(uint32_t ta_row, int c, int k0, con
   }
 }
 
+// tanh and its first two derivatives, z, d1 = 1 - z^2, d2 = -2 z d1, at two adjacent
+// columns, the arithmetic around the tanh on the packed two-lane FP32 pipe (each lane
+// rounds like the scalar instruction)
 template <int PREC>
-__device__ __forceinline__ void act_jet(float a0, float &z, float &d1, float &d2) {
+__device__ __forceinline__ void act_jet2(float2 a0, float2 &z, float2 &d1, float2 &d2) {
   if constexpr (PREC == 1) {
     // BF16 operands: the MUFU tanh (about 2^-11 relative) is below their rounding
-    z = tc::tanh_approx(a0);
-    d1 = 1.0f - z * z;
-    d2 = -2.0f * z * d1;
+    z = make_float2(tc::tanh_approx(a0.x), tc::tanh_approx(a0.y));
+    d1 = __ffma2_rn(make_float2(-z.x, -z.y), z, make_float2(1.0f, 1.0f));
+    d2 = __fmul2_rn(__fmul2_rn(z, make_float2(-2.0f, -2.0f)), d1);
   } else {
-    tanh_d(a0, z, d1, d2);   // the FP32 kernels' tanh jet (errors of a few 1e-7)
+    // the FP32 kernels' tanh jet (errors of a few 1e-7)
+    tanh_d(a0.x, z.x, d1.x, d2.x);
+    tanh_d(a0.y, z.y, d1.y, d2.y);
+  }
+}
+
+// Forward tanh jets of a thread's HC columns in place, two columns per step on the
+// packed FP32 pipe: pre-activations a[c] (c = value, t, x, xx; the value channel
+// without its bias) become z, z_t = s' a_t, z_x = s' a_x, z_xx = s'' a_x^2 + s' a_xx
+template <int C, int HC, int PREC>
+__device__ __forceinline__ void fwd_jets(float (&a)[C][HC], const float *__restrict__ bias) {
+#pragma unroll
+  for (int i = 0; i < HC; i += 2) {
+    const float2 bb = *reinterpret_cast<const float2 *>(bias + i);
+    float2 z, d1, d2;
+    act_jet2<PREC>(__fadd2_rn(make_float2(a[0][i], a[0][i + 1]), bb), z, d1, d2);
+    if constexpr (C == 4) {
+      const float2 ax = make_float2(a[2][i], a[2][i + 1]);
+      const float2 zxx = __ffma2_rn(__fmul2_rn(d2, ax), ax,
+                                    __fmul2_rn(d1, make_float2(a[3][i], a[3][i + 1])));
+      const float2 zt = __fmul2_rn(make_float2(a[1][i], a[1][i + 1]), d1);
+      const float2 zx = __fmul2_rn(ax, d1);
+      a[1][i] = zt.x;
+      a[1][i + 1] = zt.y;
+      a[2][i] = zx.x;
+      a[2][i + 1] = zx.y;
+      a[3][i] = zxx.x;
+      a[3][i + 1] = zxx.y;
+    }
+    a[0][i] = z.x;
+    a[0][i + 1] = z.y;
   }
 }
 
@@ -483,17 +516,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         else tc::tmem_ld8(D1 + lane_base + c * NC + c0, a[c]);
       }
       tc::tmem_ld_wait();
-#pragma unroll
-      for (int i = 0; i < HC; ++i) {
-        float z, d1, d2;
-        act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
-        if constexpr (C == 4) {
-          a[3][i] = d2 * a[2][i] * a[2][i] + d1 * a[3][i];
-          a[1][i] *= d1;
-          a[2][i] *= d1;
-        }
-        a[0][i] = z;
-      }
+      fwd_jets<C, HC, PREC>(a, bias_s + c0);
       if constexpr (Lay::A24_TMEM) {
 #pragma unroll
         for (int c = 0; c < C; ++c) put_act_tmem<NC, HC, PREC>(TA + lane_base, c, c0, a[c]);
@@ -536,20 +559,38 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::tmem_ld8(D3 + lane_base + c * NC + c0, wb[c]);
       }
       tc::tmem_ld_wait();
+      // two columns per step on the packed FP32 pipe
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float z, d1, d2;
-        act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
-        float ab0 = wb[0][i] * d1;
+      for (int i = 0; i < 8; i += 2) {
+        const float2 bb = *reinterpret_cast<const float2 *>(bias_s + c0 + i);
+        float2 z, d1, d2;
+        act_jet2<PREC>(__fadd2_rn(make_float2(a[0][i], a[0][i + 1]), bb), z, d1, d2);
+        float2 ab0 = __fmul2_rn(make_float2(wb[0][i], wb[0][i + 1]), d1);
         if constexpr (C == 4) {
-          const float d3 = d1 * (6.0f * z * z - 2.0f);
-          ab0 += d2 * (wb[1][i] * a[1][i] + wb[2][i] * a[2][i]) +
-                 wb[3][i] * (d3 * a[2][i] * a[2][i] + d2 * a[3][i]);
-          wb[2][i] = wb[2][i] * d1 + 2.0f * wb[3][i] * d2 * a[2][i];
-          wb[3][i] = wb[3][i] * d1;
-          wb[1][i] = wb[1][i] * d1;
+          const float2 at = make_float2(a[1][i], a[1][i + 1]);
+          const float2 ax = make_float2(a[2][i], a[2][i + 1]);
+          const float2 axx = make_float2(a[3][i], a[3][i + 1]);
+          const float2 w1 = make_float2(wb[1][i], wb[1][i + 1]);
+          const float2 w2 = make_float2(wb[2][i], wb[2][i + 1]);
+          const float2 w3 = make_float2(wb[3][i], wb[3][i + 1]);
+          // third derivative of tanh: d1 (6 z^2 - 2)
+          const float2 d3 = __fmul2_rn(d1, __ffma2_rn(__fmul2_rn(z, z), make_float2(6.0f, 6.0f),
+                                                      make_float2(-2.0f, -2.0f)));
+          ab0 = __ffma2_rn(d2, __ffma2_rn(w2, ax, __fmul2_rn(w1, at)), ab0);
+          ab0 = __ffma2_rn(w3, __ffma2_rn(__fmul2_rn(d3, ax), ax, __fmul2_rn(d2, axx)), ab0);
+          const float2 n2 = __ffma2_rn(__fmul2_rn(__fmul2_rn(w3, make_float2(2.0f, 2.0f)), d2), ax,
+                                       __fmul2_rn(w2, d1));
+          const float2 n3 = __fmul2_rn(w3, d1);
+          const float2 n1 = __fmul2_rn(w1, d1);
+          wb[1][i] = n1.x;
+          wb[1][i + 1] = n1.y;
+          wb[2][i] = n2.x;
+          wb[2][i + 1] = n2.y;
+          wb[3][i] = n3.x;
+          wb[3][i + 1] = n3.y;
         }
-        wb[0][i] = ab0;
+        wb[0][i] = ab0.x;
+        wb[0][i + 1] = ab0.y;
       }
       if constexpr (Lay::A24_TMEM) {
 #pragma unroll
@@ -622,17 +663,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           else tc::tmem_ld8(Dj + lane_base + c * NC + c0, a[c]);
         }
         tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < HC; ++i) {
-          float z, d1, d2;
-          act_jet<PREC>(a[0][i] + bias_s[c0 + i], z, d1, d2);
-          if constexpr (C == 4) {
-            a[3][i] = d2 * a[2][i] * a[2][i] + d1 * a[3][i];
-            a[1][i] *= d1;
-            a[2][i] *= d1;
-          }
-          a[0][i] = z;
-        }
+        fwd_jets<C, HC, PREC>(a, bias_s + c0);
         bool own_ok = true;
         if (j > 0) {
           // GEMM2(j - 1) has read the activations (split-BF16: its result is folded);
