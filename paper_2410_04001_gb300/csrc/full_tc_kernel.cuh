@@ -432,19 +432,30 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   // initialises R24.  Thread (row, half) takes half of each channel's RM columns.
   auto fold_chunk = [&](bool first) {
     constexpr int HR = RM / 2;
+    // each group of 8 columns: every channel's loads behind one wait, the additions on
+    // the packed FP32 pipe
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
+    for (int i0 = 0; i0 < HR; i0 += 8) {
+      float d[C][8], r[C][8];
 #pragma unroll
-      for (int i0 = 0; i0 < HR; i0 += 8) {
+      for (int c = 0; c < C; ++c) {
         const uint32_t col = lane_base + c * RM + half * HR + i0;
-        float d[8], r[8];
-        tc::tmem_ld8(D24 + col, d);
-        if (!first) tc::tmem_ld8(R24 + col, r);
-        tc::tmem_ld_wait();
+        tc::tmem_ld8(D24 + col, d[c]);
+        if (!first) tc::tmem_ld8(R24 + col, r[c]);
+      }
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
         uint32_t w8[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) w8[i] = __float_as_uint(first ? d[i] : d[i] + r[i]);
-        tc::tmem_st8(R24 + col, w8);
+        for (int i = 0; i < 8; i += 2) {
+          const float2 v = first ? make_float2(d[c][i], d[c][i + 1])
+                                 : __fadd2_rn(make_float2(d[c][i], d[c][i + 1]),
+                                              make_float2(r[c][i], r[c][i + 1]));
+          w8[i] = __float_as_uint(v.x);
+          w8[i + 1] = __float_as_uint(v.y);
+        }
+        tc::tmem_st8(R24 + lane_base + c * RM + half * HR + i0, w8);
       }
     }
     tc::tmem_st_wait();

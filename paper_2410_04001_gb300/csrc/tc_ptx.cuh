@@ -232,12 +232,18 @@ __device__ __forceinline__ void pack8_bf16(const float (&v)[8], uint4 &hi, uint4
 // nearest even; each difference is exact in FP32).
 __device__ __forceinline__ void split3_bf16x2(float a, float b, uint32_t &hi, uint32_t &mid,
                                               uint32_t &lo) {
+  // the residuals x - hi and x - hi - mid are exact in FP32, so each is one packed
+  // FMA with -1 (the same bits as a subtraction) on the two-lane FP32 pipe
+  const float2 neg1 = make_float2(-1.0f, -1.0f);
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  const float ra = a - __low2float(h), rb = b - __high2float(h);
-  const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(ra - __low2float(m), rb - __high2float(m));
   hi = *reinterpret_cast<const uint32_t *>(&h);
+  const float2 r = __ffma2_rn(make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u)),
+                              neg1, make_float2(a, b));
+  const __nv_bfloat162 m = __floats2bfloat162_rn(r.x, r.y);
   mid = *reinterpret_cast<const uint32_t *>(&m);
+  const float2 r2 = __ffma2_rn(
+      make_float2(__uint_as_float(mid << 16), __uint_as_float(mid & 0xffff0000u)), neg1, r);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(r2.x, r2.y);
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
