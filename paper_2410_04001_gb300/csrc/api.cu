@@ -346,9 +346,8 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     p.RH = 0;
     if (prec == LRNR_FP32) {
       p.pack = m->full_pack;
-      if (p.RM >= 16) {
-        // padded ranks 16 / 32 / 64: the sliced kernel, RM / 16 threads per point
-        // (full_fp32_sliced.cu)
+      if (p.RM >= 32) {
+        // padded ranks 32 / 64: RM / 16 threads share a point (full_fp32_sliced.cu)
         if (full_fp32_sl_smem_bytes(m->L, m->M, p.RM) > (size_t)kSmemBudget) return LRNR_ENOTSUP;
         p.nt = full_fp32_sl_nt(p.RM);
       } else {
@@ -402,7 +401,7 @@ lrnr_status prepare(lrnr_model *m, lrnr_form form, lrnr_precision prec, const lr
     if (m->tune_cta[LRNR_FULL][prec] > 0) per_sm = std::min(per_sm, m->tune_cta[LRNR_FULL][prec]);
     ps.grid_cap = (int)std::min<int64_t>(tiles, (int64_t)per_sm * m->num_sms);
     if (grad)
-      scr_bytes = (p.RM >= 16 ? full_fp32_sl_scratch_floats(m->L, p.RM, ps.grid_cap)
+      scr_bytes = (p.RM >= 32 ? full_fp32_sl_scratch_floats(m->L, p.RM, ps.grid_cap)
                               : full_fp32_scratch_floats(m->L, p.RM, p.nt, ps.grid_cap)) *
                   sizeof(float);
   }

@@ -372,7 +372,7 @@ int full_fp32_choose_nt(int L, int RM, int P) {
 }
 
 int full_fp32_ctas_per_sm(const KParams &p) {
-  if (p.RM >= 16) return full_fp32_sl_ctas_per_sm(p);
+  if (p.RM >= 32) return full_fp32_sl_ctas_per_sm(p);
   if (p.nt == 64) {
     if (p.RM == 8) return ctas_per_sm_t<8, 64>(p);
     if (p.RM == 16) return ctas_per_sm_t<16, 64>(p);
@@ -383,10 +383,10 @@ int full_fp32_ctas_per_sm(const KParams &p) {
   return 1;
 }
 
-// Padded rank 8: one thread per point (this file); 16, 32 and 64: the sliced kernel,
-// RM / 16 threads per point.
+// Padded ranks 8 and 16: one thread per point (this file); 32 and 64: the sliced
+// kernel, RM / 16 threads per point.
 cudaError_t launch_full_fp32(const KParams &p, int grid, cudaStream_t st) {
-  if (p.RM >= 16) return launch_full_fp32_sl(p, grid, st);
+  if (p.RM >= 32) return launch_full_fp32_sl(p, grid, st);
   if (!p.scratch && p.grad) return cudaErrorInvalidValue;
   if (p.nt == 64) {
     if (p.RM == 8) return launch_full_t<8, 64>(p, grid, st);

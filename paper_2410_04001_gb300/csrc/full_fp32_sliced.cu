@@ -1,13 +1,10 @@
-// Full-width LRNR residual + adjoint in FP32 for padded ranks 16, 32 and 64 (Sec. 2.1
+// Full-width LRNR residual + adjoint in FP32 for padded ranks 32 and 64 (Sec. 2.1
 // Eq. 2.1-2.2, Sec. 2.3): the paper's convection-diffusion-reaction network
-// r = (1, 49, 30, 25, 1) pads to 64, the adjoint-stress network to 32, the CDR
-// workload network to 16.
+// r = (1, 49, 30, 25, 1) pads to 64, the adjoint-stress network to 32.
 //
-// A point's rank-r jets do not fit in one thread's registers above rank 16 (two jets
+// A point's rank-r jets do not fit in one thread's registers at these ranks (two jets
 // of 4 channels x RM floats are live through a layer), so TPP = RM / 16 consecutive
-// threads share a point (at rank 16 one thread holds the whole point; this kernel's
-// organisation, 128 points per tile and the rank-r jets as 16-entry slices, measured
-// 10 % faster there than the one-thread kernel of full_fp32.cu): thread q of the point holds entries [16 q, 16 q + 16) of
+// threads share a point: thread q of the point holds entries [16 q, 16 q + 16) of
 // every rank-r jet of the point.  Per row i of a layer:
 //   a_i  = sum over the slices of U_i . (s * q)   (partial dot products, completed by
 //                                                  log2(TPP) shuffles; every thread of
@@ -431,7 +428,6 @@ size_t full_fp32_sl_scratch_floats(int L, int RM, int grid) {
 }
 
 int full_fp32_sl_ctas_per_sm(const KParams &p) {
-  if (p.RM == 16) return sl_ctas_per_sm_t<16, 1>(p);
   if (p.RM == 32) return sl_ctas_per_sm_t<32, 2>(p);
   if (p.RM == 64) return sl_ctas_per_sm_t<64, 4>(p);
   return 1;
@@ -440,7 +436,6 @@ int full_fp32_sl_ctas_per_sm(const KParams &p) {
 cudaError_t launch_full_fp32_sl(const KParams &p, int grid, cudaStream_t st) {
   if (!p.scratch && p.grad) return cudaErrorInvalidValue;
   if (p.nt != full_fp32_sl_nt(p.RM)) return cudaErrorInvalidValue;
-  if (p.RM == 16) return launch_sl_t<16, 1>(p, grid, st);
   if (p.RM == 32) return launch_sl_t<32, 2>(p, grid, st);
   if (p.RM == 64) return launch_sl_t<64, 4>(p, grid, st);
   return cudaErrorInvalidValue;
