@@ -59,3 +59,16 @@ def test_build_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.lrnr_build(2, 8, None, None, None, None, ctypes.byref(out)) == 1
     r = (ctypes.c_int * 3)(2, 40, 1)   # rank above 32
     assert lib.lrnr_build(2, 8, r, None, None, None, ctypes.byref(out)) == 1
+
+
+def test_copy_pinned_checks_arguments_before_any_cuda_call(lib):
+    """lrnr_copy_pinned: an empty copy succeeds and a null pointer with bytes > 0 is
+    refused, both before the library asks CUDA about the pointers."""
+    f = lib.lrnr_copy_pinned
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    buf = ctypes.create_string_buffer(64)
+    assert f(None, None, 0, None) == 0
+    assert f(ctypes.addressof(buf), ctypes.addressof(buf), 0, None) == 0
+    assert f(None, ctypes.addressof(buf), 64, None) == 1
+    assert f(ctypes.addressof(buf), None, 64, None) == 1
