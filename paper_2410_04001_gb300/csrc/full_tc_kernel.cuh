@@ -137,8 +137,11 @@ struct TcLayout {
 // device status set) if the wait timed out.  The expected parity advances only on
 // success, so that after a timeout the drain at the end of the kernel waits for the
 // very phase (the MMA or copy still in flight) that timed out.
-__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, bool &pend, const KParams &p) {
-  const bool ok = tc::mbar_wait(bar, ph, p.max_wait);
+// A thread whose own earlier wait failed (ok_before false) does not wait and votes for
+// the failure.
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t &ph, bool &pend, const KParams &p,
+                                         bool ok_before = true) {
+  const bool ok = ok_before && tc::mbar_wait(bar, ph, p.max_wait);
   const bool all = __syncthreads_and(ok);
   if (all) {
     ph ^= 1u;
@@ -481,6 +484,9 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
   auto wait_b = [&](int n) {
     return wait_bar(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], ctl.pb[n % Lay::NB], p);
   };
+  auto wait_b_own = [&](int n) {
+    return wait_own(&ctl.bb[n % Lay::NB], ctl.phb[n % Lay::NB], ctl.pb[n % Lay::NB], p);
+  };
 
   // MMA issue (thread 0) for the chunk whose bases are in B buffer n
   // forward GEMM1: a_c = (s q_c) U_chunk^T into the accumulator at column D
@@ -723,10 +729,11 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::mma_commit(ctl.b1);
       }
       ctl.p1 = true;
+      bool b_ok = true;   // this thread's own wait for the next chunk's bases
       for (int j = 0; j < NCH; ++j) {
         const int n = n0 + j;
-        // GEMM1(j) done, and with it GEMM2(j - 1)
-        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+        // GEMM1(j) done, and with it GEMM2(j - 1); a failed wait for B(j) is agreed on here
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p, b_ok)) { dead = true; return; }
         if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
         if (j >= 1 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
         fwd_epilogue(n);
@@ -738,18 +745,22 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           issue_g24(n, j, 3 * PK::T);
         }
         if (j + 1 < NCH) {
-          if (!wait_b(n + 1)) {
+          // every thread waits for B(j + 1) on its own, without a CTA barrier: the MMA
+          // issuers before GEMM1(j + 1), the others before the next epilogue reads the
+          // chunk's biases
+          b_ok = wait_b_own(n + 1);
+          if (b_ok) {
+            if (issuer) {
+              issue_g1(n + 1);
+              tc::mma_commit(ctl.b1);
+            }
+            ctl.p1 = true;
+          } else {
             // GEMM2(j) is in flight: commit it for the drain
             if (issuer) tc::mma_commit(ctl.b2);
             ctl.p2 = true;
-            dead = true;
-            return;
           }
-          if (issuer) {
-            issue_g1(n + 1);
-            tc::mma_commit(ctl.b1);
-          }
-          ctl.p1 = true;
+          __syncwarp();
         } else {
           if (issuer) tc::mma_commit(ctl.b2);
           ctl.p2 = true;
@@ -870,10 +881,12 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         tc::mma_commit(ctl.b1);
       }
       ctl.p1 = true;
+      bool b_ok = true;   // this thread's own wait for the next chunk's bases
       for (int j = 0; j < NCH; ++j) {
         const int n = n0 + j;
-        // GEMM1 / GEMM3 (j) done, and with them GEMM4(j - 1)
-        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }
+        // GEMM1 / GEMM3 (j) done, and with them GEMM4(j - 1); a failed wait for B(j) is
+        // agreed on here
+        if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p, b_ok)) { dead = true; return; }
         if constexpr (Lay::SPLIT) if (j > 0) fold_chunk(j == 1);
         if (j >= 1 && j + 1 < NCH) fetch(lp, j + 1, n + 1);
         rev_epilogue(n);
@@ -893,18 +906,20 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           if (col < M) prow[DB0 + l * M + col] = v;
         }
         if (j + 1 < NCH) {
-          if (!wait_b(n + 1)) {
+          // each thread's own wait for B(j + 1), as in the forward sweep
+          b_ok = wait_b_own(n + 1);
+          if (b_ok) {
+            if (issuer) {
+              issue_g13(n + 1);
+              tc::mma_commit(ctl.b1);
+            }
+            ctl.p1 = true;
+          } else {
             // GEMM4(j) is in flight: commit it for the drain
             if (issuer) tc::mma_commit(ctl.b2);
             ctl.p2 = true;
-            dead = true;
-            return;
           }
-          if (issuer) {
-            issue_g13(n + 1);
-            tc::mma_commit(ctl.b1);
-          }
-          ctl.p1 = true;
+          __syncwarp();
         } else {
           if (issuer) tc::mma_commit(ctl.b2);
           ctl.p2 = true;
