@@ -661,14 +661,20 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         const int n = n0 + j;
         if (!wait_bar(ctl.b1, ctl.ph1, ctl.p1, p)) { dead = true; return; }   // GEMM1(j) done
         if (j + 2 < NCH) fetch(lp, j + 2, n + 2);
+        bool b_ok = true;
         if (j + 1 < NCH) {
-          if (!wait_b(n + 1)) { dead = true; return; }
-          if (issuer) {
-            issue_g1d(n + 1, dacc(j + 1));
-            tc::mma_commit(ctl.b1);
+          // every thread waits for B(j + 1) on its own (the issuers before GEMM1(j + 1),
+          // the others before the next epilogue reads the biases); the CTA agrees on a
+          // timeout at the barrier below
+          b_ok = wait_b_own(n + 1);
+          if (b_ok) {
+            if (issuer) {
+              issue_g1d(n + 1, dacc(j + 1));
+              tc::mma_commit(ctl.b1);
+            }
+            ctl.p1 = true;
           }
           __syncwarp();   // the warp reconverges before the tensor-memory loads below
-          ctl.p1 = true;
         }
         const float *bias_s = reinterpret_cast<const float *>(bbuf(n) + 4 * PK::T);
         const uint32_t Dj = dacc(j);
@@ -705,7 +711,7 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
-        if (__syncthreads_or(!own_ok)) { dead = true; return; }
+        if (__syncthreads_or(!own_ok || !b_ok)) { dead = true; return; }
         if (issuer) {
           tc::fence_after_sync();
           issue_g24(n, j, 3 * PK::T);
