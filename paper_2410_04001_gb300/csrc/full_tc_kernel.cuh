@@ -903,14 +903,6 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           tc::fence_after_sync();
           issue_g24(n, j, 2 * PK::T);
         }
-        if (tid < NC) {
-          // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
-          const int h = tid / HC, cc = tid % HC;
-          const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
-                          dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
-          const int col = j * NC + tid;
-          if (col < M) prow[DB0 + l * M + col] = v;
-        }
         if (j + 1 < NCH) {
           // each thread's own wait for B(j + 1), as in the forward sweep
           b_ok = wait_b_own(n + 1);
@@ -930,6 +922,17 @@ __device__ void tc_tile(const KParams &p, const Tile &T, int tile, unsigned char
           if (issuer) tc::mma_commit(ctl.b2);
           ctl.p2 = true;
         }
+        // the chunk's dL/db columns, after the MMA issue (thread 0 issues too); the
+        // partial sums in dbw are rewritten only after the next CTA-wide wait
+        if (tid < NC) {
+          // column tid of the chunk: warps (0..3) hold the first half, (4..7) the second
+          const int h = tid / HC, cc = tid % HC;
+          const float v = dbw[(4 * h + 0) * HC + cc] + dbw[(4 * h + 1) * HC + cc] +
+                          dbw[(4 * h + 2) * HC + cc] + dbw[(4 * h + 3) * HC + cc];
+          const int col = j * NC + tid;
+          if (col < M) prow[DB0 + l * M + col] = v;
+        }
+        __syncwarp();
       }
     } else {
       fetch(lp, 0, n0);
