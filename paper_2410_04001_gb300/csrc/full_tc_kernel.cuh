@@ -37,7 +37,9 @@
 // earlier still, into D3 and D1 in turn, so that it runs during the epilogue of chunk
 // j.  The bases are packed chunk by chunk in the operand layout (no-swizzle K-major
 // core matrices) so that one cp.async.bulk moves a chunk; later chunks are copied
-// while earlier ones are processed (two or four buffers where shared memory allows).
+// while earlier ones are processed (two or four buffers where shared memory allows),
+// and in those loops every thread waits for the next chunk's copy on its own, the CTA
+// agreeing on a timeout at its next barrier.
 // The rank-r layer inputs q (FP32) are kept in a per-CTA global scratch area (it stays
 // in L2) for the reverse sweep.  Every mbarrier wait is bounded.
 #pragma once
