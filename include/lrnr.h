@@ -16,11 +16,13 @@
  *          U^l is M_l x r[l], V^l is M_{l-1} x r[l] (V has as many rows as the
  *          layer's input; the printed M_l rows cannot multiply z^{l-1}).
  *          Constraints: 1 <= r[0] <= 2, 1 <= r[l] <= 64 for 0 < l < L, r[L] == 1.
- *          Ranks are padded to 8, 16, 32 or 64.  Full-width FP32 takes padded ranks
- *          up to 32; FastLRNR FP32 takes any padded rank with rhat <= 16 (ranks 32
- *          and 64 through reduced coordinates, Eq. 2.8 regrouped per layer); the
- *          full-width network at rank 64 runs in LRNR_BF16 on the tensor cores
- *          only; other combinations return LRNR_ENOTSUP.
+ *          Ranks are padded to 8, 16, 32 or 64.  Full-width FP32 takes every padded
+ *          rank (at 32 and 64 a point is spread over rank / 16 threads); FastLRNR
+ *          FP32 takes any padded rank with rhat <= 16 (ranks 32 and 64 through
+ *          reduced coordinates, Eq. 2.8 regrouped per layer); on the tensor cores
+ *          the full-width network at rank 64 runs in LRNR_BF16 only; other
+ *          combinations, and shapes whose per-CTA shared memory would not fit,
+ *          return LRNR_ENOTSUP.
  *   s      coefficients, per PDE instance a vector of sum(r) floats, layer-major.
  *   b      biases, b^l of length M_l; sum over layers = L*M + 1 ("sum_m").
  *   mu     (beta, nu, rho): N[u] = u_t + beta u_x - nu u_xx - rho u (1-u)
